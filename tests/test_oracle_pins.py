@@ -1,0 +1,411 @@
+"""Pins of the oracle against facts fixed by the paper and by mathematics.
+
+Each test compares the oracle with something that is not the oracle:
+published known-answer vectors, closed forms, the exact Fock-space trace of
+Eq. (2), brute-force sums over all fields of Eq. (3), direct determinants,
+finite differences, and symmetry identities of the half-filled bipartite
+model.  None of these recomputes an oracle formula a second way.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import dqmc as o
+from tests import enumerate_fields as en
+from tests import fock
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10: known-answer vectors published with the Random123 library
+# (Salmon et al., SC'11), stored in tests/golden/philox4x32_10_kat.txt.
+# --------------------------------------------------------------------------
+def _kat_rows():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "philox4x32_10_kat.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if len(line) == 10:
+            rows.append([int(v, 16) for v in line])
+    assert rows
+    return rows
+
+
+def test_philox_known_answers():
+    for r in _kat_rows():
+        ctr, key, out = r[0:4], r[4:6], r[6:10]
+        assert list(o.philox4x32_10(ctr, key)) == out
+
+
+def test_philox_vectorised_matches_scalar():
+    rng = np.random.default_rng(1)
+    c = rng.integers(0, 2**32, size=(4, 50), dtype=np.uint64)
+    k = (0x12345678, 0x9ABCDEF0)
+    vec = o.philox4x32_10_np(c[0], c[1], c[2], c[3], *k)
+    for j in range(50):
+        assert tuple(int(v[j]) for v in vec) == o.philox4x32_10(tuple(int(x) for x in c[:, j]), k)
+
+
+def test_uniform53_edges():
+    assert o.uniform53(0, 0) == 0.0
+    top = float(o.uniform53(0xFFFFFFFF, 0xFFFFFFFF))
+    assert top < 1.0 and top == 1.0 - 2.0 ** -53
+
+
+def test_initial_field_is_balanced_and_seeded():
+    f0 = o.initial_field(0, 0, 64, 100)
+    f1 = o.initial_field(0, 1, 64, 100)
+    assert set(np.unique(f0)) == {-1, 1}
+    assert abs(f0.mean()) < 0.05
+    assert (f0 != f1).any()
+    assert (o.initial_field(0, 0, 64, 100) == f0).all()
+
+
+# --------------------------------------------------------------------------
+# Eq. (1): lattice and hopping.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("Lx,Ly", [(2, 2), (3, 2), (4, 4), (6, 4), (5, 3)])
+def test_hopping_spectrum_is_cosine_band(Lx, Ly):
+    K = o.hopping_matrix(Lx, Ly, 0.25)
+    ev = np.sort(np.linalg.eigvalsh(K))
+    closed = np.sort(-2 * 0.25 * np.add.outer(np.cos(2 * np.pi * np.arange(Ly) / Ly),
+                                              np.cos(2 * np.pi * np.arange(Lx) / Lx)).ravel())
+    np.testing.assert_allclose(ev, closed, atol=1e-13)
+    np.testing.assert_allclose(np.sort(o.dispersion(Lx, Ly, 0.25)), closed, atol=1e-13)
+
+
+def test_hopping_matches_fock_bond_list():
+    K = o.hopping_matrix(4, 2, 0.3)
+    K2 = np.zeros_like(K)
+    for j, i in fock.bonds(4, 2):
+        K2[j, i] -= 0.3
+    assert np.array_equal(K, K2)
+
+
+@pytest.mark.parametrize("Lx,Ly", [(2, 2), (4, 4), (6, 2)])
+def test_bipartite_sign_flips_hopping(Lx, Ly):
+    K = o.hopping_matrix(Lx, Ly, 0.25)
+    P = np.diag(o.sublattice_sign(Lx, Ly))
+    np.testing.assert_array_equal(P @ K @ P, -K)
+
+
+def test_exp_hopping_against_expm():
+    K = o.hopping_matrix(4, 4, 0.25)
+    E, Einv = o.exp_hopping(K, 0.125)
+    np.testing.assert_allclose(E, scipy.linalg.expm(-0.125 * K), atol=1e-14)
+    np.testing.assert_allclose(E @ Einv, np.eye(16), atol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Sec. 2: discrete Hubbard-Stratonovich transform.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("U,dtau", [(1.0, 0.25), (2.0, 0.125), (3.0, 0.1), (8.0, 0.05)])
+def test_hs_identity(U, dtau):
+    lam = o.hs_lambda(U, dtau)
+    C = o.hs_prefactor(U, dtau)
+    for nu in (0, 1):
+        for nd in (0, 1):
+            lhs = math.exp(-dtau * U * (nu - 0.5) * (nd - 0.5))
+            rhs = C * sum(math.exp(lam * s * (nu - nd)) for s in (-1, 1))
+            assert rhs == pytest.approx(lhs, rel=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Eq. (3) against Eq. (2): brute-force field sum == exact Trotter trace.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("Lx,Ly,t,U,dtau,L", [
+    (2, 2, 0.25, 2.0, 0.25, 3),
+    (2, 2, 0.25, 1.0, 0.5, 4),
+    (2, 2, 0.4, 4.0, 0.2, 2),
+    (2, 2, 0.25, 0.0, 0.25, 3),
+    (3, 2, 0.25, 2.0, 0.25, 2),
+    (2, 2, 0.25, 2.0, 0.1, 5),
+])
+def test_partition_function_enumeration_vs_fock(Lx, Ly, t, U, dtau, L):
+    p = o.Params(Lx, Ly, t, U, L * dtau, dtau, n_s=2)
+    _, _, Z, _ = en.enumerate_sum(p)
+    Zf = fock.trotter_trace_sectors(Lx, Ly, t, U, dtau, L)
+    assert Z == pytest.approx(Zf, rel=1e-12)
+
+
+def test_fock_full_and_sector_traces_agree():
+    F = fock.FockHubbard(2, 2, 0.25, 2.0, 0.25, 3)
+    assert F.Z == pytest.approx(fock.trotter_trace_sectors(2, 2, 0.25, 2.0, 0.25, 3), rel=1e-12)
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    """2x2 cluster, L = 3: every field (4096) and the exact Fock space."""
+    p = o.Params(2, 2, 0.25, 2.0, 0.75, 0.25, n_s=2)
+    fields, w, Z, greens = en.enumerate_sum(p, want_g=True)
+    F = fock.FockHubbard(2, 2, 0.25, 2.0, 0.25, 3)
+    return p, fields, w, greens, F
+
+
+def test_equal_time_observables_enumeration_vs_fock(tiny):
+    p, fields, w, greens, F = tiny
+    obs = np.array([o.observables_from_g(greens[1][f], greens[-1][f], p.K) for f in range(len(w))])
+    mean = (w[:, None] * obs).sum(0) / w.sum()
+    assert mean[0] == pytest.approx(1.0, abs=1e-13)
+    assert mean[1] == pytest.approx(F.docc(), rel=1e-11)
+    assert mean[2] == pytest.approx(F.ekin(), rel=1e-11)
+
+
+@pytest.mark.parametrize("l", [0, 1, 2, 3])
+def test_unequal_time_green_enumeration_vs_fock(tiny, l):
+    """Weighted field average of the oracle's G(l,0) == Tr[T^{L-l} c_i T^l c_j^dag]/Z."""
+    p, fields, w, _, F = tiny
+    acc = np.zeros((p.N, p.N))
+    for f in range(len(w)):
+        ch = o.Chain(p, field=fields[f])
+        acc += w[f] * ch.gtau_matrices(1)[l]
+    np.testing.assert_allclose(acc / w.sum(), F.gtau_up(l), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Metropolis ratio and Sherman-Morrison update against direct determinants.
+# --------------------------------------------------------------------------
+def _direct_M(p, field, sigma):
+    A = np.eye(p.N)
+    for l in range(p.L):
+        A = o.b_matrix(p.E, p.lam, sigma, field[l]) @ A
+    return np.eye(p.N) + A
+
+
+def test_metropolis_ratio_and_update_vs_determinants():
+    p = o.Params(4, 2, 0.25, 2.0, 1.0, 0.25, n_s=2)
+    ch = o.Chain(p, seed=3)
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        l = int(rng.integers(1, p.L + 1))
+        i = int(rng.integers(0, p.N))
+        for sg in (1, -1):
+            G = ch.green(l - 1, sg)
+            s = float(ch.field[l - 1, i])
+            delta = math.exp(-2 * sg * p.lam * s) - 1
+            R = 1 + delta * (1 - G[i, i])
+            f2 = ch.field.copy()
+            f2[l - 1, i] *= -1
+            # det M'/det M with slice l rotated to the right end (cyclic invariance)
+            rot = np.concatenate([ch.field[l - 1:], ch.field[:l - 1]])
+            rot2 = np.concatenate([f2[l - 1:], f2[:l - 1]])
+            ratio = np.linalg.det(_direct_M(p, rot2, sg)) / np.linalg.det(_direct_M(p, rot, sg))
+            assert R == pytest.approx(ratio, rel=1e-12)
+            col = -G[:, i].copy()
+            col[i] += 1
+            Gn = G - (delta / R) * np.outer(col, G[i, :])
+            ch2 = o.Chain(p, field=f2)
+            np.testing.assert_allclose(Gn, ch2.green(l - 1, sg), atol=1e-12)
+
+
+def test_sweep_running_green_matches_fresh():
+    """After each slice the wrapped, updated G equals the freshly stabilised G."""
+    p = o.Params(4, 4, 0.25, 2.0, 2.0, 0.125, n_s=4)
+    ch = o.Chain(p, seed=1)
+    out = ch.sweep()
+    assert out["accepted"] > 0
+    assert out["drift"] < 1e-10
+    np.testing.assert_allclose(out["G_up"], ch.green(p.L, 1), atol=1e-12)
+
+
+def test_wrap_identity():
+    p = o.Params(4, 2, 0.25, 2.0, 1.0, 0.25, n_s=2)
+    ch = o.Chain(p, seed=5)
+    for l in range(1, p.L + 1):
+        for sg in (1, -1):
+            G = ch.B(l, sg) @ ch.green(l - 1, sg) @ ch.Binv(l, sg)
+            np.testing.assert_allclose(G, ch.green(l, sg), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Stabilisation.
+# --------------------------------------------------------------------------
+def test_stable_green_equals_naive_inverse_at_small_beta():
+    p = o.Params(4, 4, 0.25, 2.0, 1.0, 0.125, n_s=3)
+    ch = o.Chain(p, seed=2)
+    for sg in (1, -1):
+        np.testing.assert_allclose(ch.green(0, sg), np.linalg.inv(_direct_M(p, ch.field, sg)),
+                                   atol=1e-12)
+
+
+def test_stable_green_independent_of_grouping_at_large_beta():
+    """At beta = 20 the naive product is singular in FP64; two stabilisation
+    intervals must still agree."""
+    G = []
+    for n_s in (2, 8):
+        p = o.Params(4, 4, 0.25, 2.0, 20.0, 0.125, n_s=n_s)
+        G.append(o.Chain(p, seed=4).green(37, 1))
+    np.testing.assert_allclose(G[0], G[1], atol=1e-10)
+    assert np.all(np.isfinite(G[0]))
+
+
+def test_two_stack_green_matches_cyclic_chain():
+    p = o.Params(4, 4, 0.25, 2.0, 10.0, 0.125, n_s=8)
+    ch = o.Chain(p, seed=7)
+    for l in (0, 24, 40, p.L):
+        G, _, _ = o.two_stack_green(ch.right_udv(l, 1), ch.left_udv(l, 1))
+        np.testing.assert_allclose(G, ch.green(l, 1), atol=1e-11)
+
+
+def test_two_stack_unequal_time_matches_direct_products():
+    """G(l,0) = R_l G(0) and Y = (I - G(0)) R_l^{-1} by direct products (small beta)."""
+    p = o.Params(4, 4, 0.25, 2.0, 1.0, 0.125, n_s=3)
+    ch = o.Chain(p, seed=8)
+    G0 = np.linalg.inv(_direct_M(p, ch.field, 1))
+    for l in (0, 3, 5, p.L):
+        R = np.eye(p.N)
+        for m in range(1, l + 1):
+            R = ch.B(m, 1) @ R
+        _, Gl0, Y = o.two_stack_green(ch.right_udv(l, 1), ch.left_udv(l, 1))
+        np.testing.assert_allclose(Gl0, R @ G0, atol=1e-12)
+        np.testing.assert_allclose(Y, (np.eye(p.N) - G0) @ np.linalg.inv(R), atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# U = 0 closed form: lambda = 0, no Trotter error.
+# --------------------------------------------------------------------------
+def test_u0_closed_form_gtau_and_ratios():
+    p = o.Params(4, 4, 0.25, 0.0, 4.0, 0.25, n_s=4)
+    ch = o.Chain(p, seed=0)
+    eps = o.dispersion(4, 4, 0.25)
+    gt = ch.gtau()
+    for l in range(p.L + 1):
+        tau = l * p.dtau
+        closed = np.exp(-tau * eps) / (1 + np.exp(-p.beta * eps))
+        np.testing.assert_allclose(gt[l], closed, atol=1e-13)
+    out = ch.sweep()
+    np.testing.assert_allclose(out["ratios"], 1.0, atol=1e-14)
+    assert out["accepted"] == p.N * p.L
+    ekin = out["obs"][-1][2]
+    exact = 2 * np.sum(eps / (1 + np.exp(p.beta * eps))) / p.N
+    assert ekin == pytest.approx(exact, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Atomic limit t = 0: no Trotter error; per-site closed form.
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("U,beta,dtau", [(2.0, 1.0, 0.25), (4.0, 0.5, 0.125)])
+def test_atomic_limit_enumeration(U, beta, dtau):
+    p = o.Params(2, 2, 0.0, U, beta, dtau, n_s=2)
+    if p.N * p.L > 20:
+        pytest.skip("too many fields")
+    fields, w, Z, greens = en.enumerate_sum(p, want_g=True)
+    docc = np.array([o.observables_from_g(greens[1][f], greens[-1][f], p.K)[1] for f in range(len(w))])
+    d_exact = math.exp(-beta * U / 4) / (2 * math.exp(-beta * U / 4) + 2 * math.exp(beta * U / 4))
+    assert (w * docc).sum() / w.sum() == pytest.approx(d_exact, rel=1e-12)
+    z_site = 2 * math.exp(-beta * U / 4) + 2 * math.exp(beta * U / 4)
+    assert Z == pytest.approx(z_site ** p.N, rel=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Half filling on a bipartite lattice (the paper's case): particle-hole.
+# --------------------------------------------------------------------------
+def test_particle_hole_identities():
+    p = o.Params(4, 4, 0.25, 2.0, 4.0, 0.125, n_s=5)
+    ch = o.Chain(p, seed=9)
+    P = np.diag(o.sublattice_sign(4, 4))
+    for l in (0, 7, 20, p.L):
+        Gu, Gd = ch.green(l, 1), ch.green(l, -1)
+        np.testing.assert_allclose(Gd, np.eye(p.N) - P @ Gu.T @ P, atol=1e-12)
+        assert o.observables_from_g(Gu, Gd, p.K)[0] == pytest.approx(1.0, abs=1e-12)
+    lu, su = ch.logdet(1)
+    ld, sd = ch.logdet(-1)
+    assert ld - lu == pytest.approx(-p.lam * ch.field.astype(float).sum(), abs=1e-9)
+    assert su * sd > 0
+
+
+def test_gtau_boundary_sum():
+    p = o.Params(4, 4, 0.25, 2.0, 2.0, 0.25, n_s=4)
+    ch = o.Chain(p, seed=11)
+    gt = ch.gtau()
+    np.testing.assert_allclose(gt[0] + gt[-1], 1.0, atol=1e-12)
+
+
+def test_gtau_spin_down_from_spin_up_backward_propagator():
+    """Per configuration, G_dn(l,0) = P [(I - G_up(0)) R_l^{-1}]^T P, so the
+    spin-down momentum diagonal at k is that of Y_l = (I - G_up(0)) R_l^{-1}
+    at k + Q, Q = (pi, pi)."""
+    Lx = Ly = 4
+    p = o.Params(Lx, Ly, 0.25, 2.0, 4.0, 0.125, n_s=5)
+    ch = o.Chain(p, seed=12)
+    P = np.diag(o.sublattice_sign(Lx, Ly))
+    kq = [((i % Lx + Lx // 2) % Lx) + Lx * (((i // Lx) + Ly // 2) % Ly) for i in range(p.N)]
+    gdn = ch.gtau_matrices(-1)
+    for l in (0, 5, 13, p.L):
+        _, _, Y = o.two_stack_green(ch.right_udv(l, 1), ch.left_udv(l, 1))
+        np.testing.assert_allclose(gdn[l], P @ Y.T @ P, atol=1e-11)
+        np.testing.assert_allclose(o.momentum_diag(gdn[l], Lx, Ly),
+                                   o.momentum_diag(Y, Lx, Ly)[kq], atol=1e-11)
+
+
+def test_gtau_ensemble_ph_symmetry_by_enumeration():
+    """<G_k(tau)> = <G_{k+Q}(beta - tau)> over all fields (2x2, L = 3)."""
+    p = o.Params(2, 2, 0.25, 2.0, 0.75, 0.25, n_s=2)
+    fields, w, _, _ = en.enumerate_sum(p)
+    acc = np.zeros((p.L + 1, p.N))
+    for f in range(len(w)):
+        acc += w[f] * o.Chain(p, field=fields[f]).gtau()
+    acc /= w.sum()
+    kq = [((i % 2 + 1) % 2) + 2 * (((i // 2) + 1) % 2) for i in range(4)]
+    np.testing.assert_allclose(acc[:, kq], acc[::-1, :], atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Derivatives of log W.
+# --------------------------------------------------------------------------
+def _logw_with(Lx, Ly, t, U, beta, dtau, field, lam=None):
+    p = o.Params(Lx, Ly, t, U, beta, dtau, n_s=4)
+    if lam is not None:
+        p.lam = lam
+    return o.Chain(p, field=field).logw()
+
+
+def test_gradients_vs_central_differences():
+    Lx, Ly, t, U, beta, dtau = 4, 2, 0.25, 2.0, 2.0, 0.125
+    p = o.Params(Lx, Ly, t, U, beta, dtau, n_s=4)
+    ch = o.Chain(p, seed=13)
+    dt, dlam = ch.grad()
+    h = 1e-5
+    fd_t = (_logw_with(Lx, Ly, t + h, U, beta, dtau, ch.field)
+            - _logw_with(Lx, Ly, t - h, U, beta, dtau, ch.field)) / (2 * h)
+    fd_l = (_logw_with(Lx, Ly, t, U, beta, dtau, ch.field, p.lam + h)
+            - _logw_with(Lx, Ly, t, U, beta, dtau, ch.field, p.lam - h)) / (2 * h)
+    assert dt == pytest.approx(fd_t, rel=1e-7)
+    assert dlam == pytest.approx(fd_l, rel=1e-7)
+
+
+def test_t_gradient_expectation_is_hellmann_feynman():
+    """<d log W/dt> over all fields == d ln Z_dtau/dt of the Fock trace."""
+    Lx, Ly, t, U, dtau, L = 2, 2, 0.25, 2.0, 0.25, 3
+    p = o.Params(Lx, Ly, t, U, L * dtau, dtau, n_s=2)
+    fields, w, Z, _ = en.enumerate_sum(p)
+    g = np.array([o.Chain(p, field=fields[f]).grad()[0] for f in range(len(w))])
+    h = 1e-5
+    zp = fock.trotter_trace_sectors(Lx, Ly, t + h, U, dtau, L)
+    zm = fock.trotter_trace_sectors(Lx, Ly, t - h, U, dtau, L)
+    assert (w * g).sum() / w.sum() == pytest.approx((math.log(zp) - math.log(zm)) / (2 * h), rel=1e-7)
+
+
+# --------------------------------------------------------------------------
+# Monte Carlo statistics: the Markov chain samples Eq. (3).
+# --------------------------------------------------------------------------
+def test_mc_double_occupancy_and_kinetic_energy_vs_exact():
+    Lx, Ly, t, U, dtau, L = 2, 2, 0.25, 2.0, 0.25, 4
+    F = fock.FockHubbard(Lx, Ly, t, U, dtau, L)
+    p = o.Params(Lx, Ly, t, U, L * dtau, dtau, n_s=2)
+    samples = []
+    for c in range(4):
+        ch = o.Chain(p, seed=100, chain=c)
+        for _ in range(30):
+            ch.sweep(measure=False)
+        for _ in range(250):
+            samples.append(np.mean(ch.sweep()["obs"], axis=0))
+    s = np.array(samples).reshape(4, -1, 3)
+    bins = s.reshape(4, 25, 10, 3).mean(axis=2).reshape(-1, 3)
+    mean = bins.mean(0)
+    err = bins.std(0, ddof=1) / math.sqrt(len(bins))
+    assert abs(mean[1] - F.docc()) < 4 * err[1]
+    assert abs(mean[2] - F.ekin()) < 4 * err[2]
+    assert np.allclose(s[..., 0], 1.0, atol=1e-12)
