@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark: Hubbard-Stratonovich field updates per second of the BSS-DQMC
+sweep on one GB300, 16x16 cluster, mixed precision against plain FP64.
+
+Workload (one "step" = one sweep of every chain over all L slices, with the
+Metropolis pass, delayed rank-k updates, slice wraps, UDV stack products,
+FP64 QR stabilisation and G recompute at every stabilisation point,
+equal-time observables, the left-stack rebuild and the unequal-time G(k, tau)
+of every chain): 16x16 periodic cluster, t = 0.25, U = 2, beta = 20,
+dtau = 0.125 (L = 160), 64 independent chains, delay k = 32, stabilisation
+every 10 slices.  Updates counted = chains * N * L proposals per sweep.
+
+The working set (UDV stacks of 64 chains, 2.2 GB) is far larger than the
+129 MB L2, so no L2 flush is needed between steps.
+
+`--impl reference` times the CPU oracle (oracle/, plain FP64 numpy) on the
+host cores instead: each step sweeps one chain per worker process.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HS-field updates/s on 1 GB300 at 16x16; mixed/batched vs plain FP64 at equal G error"
+UNIT = "updates/s"
+W = dict(Lx=16, Ly=16, t=0.25, U=2.0, beta=20.0, dtau=0.125, chains=64, ns=10, k=32)
+WORKLOAD = ("16x16 periodic Hubbard, t=0.25, U=2, beta=20, dtau=0.125 (L=160), 64 chains, "
+            "k=32, n_s=10, G(k,tau) every sweep")
+
+
+def n_sites():
+    return W["Lx"] * W["Ly"]
+
+
+def n_slices():
+    return int(round(W["beta"] / W["dtau"]))
+
+
+def updates_per_sweep(chains):
+    return chains * n_sites() * n_slices()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (host cores): one worker process per core, each sweeps
+# one chain of the workload once; started with `spawn` before any CUDA call.
+# ---------------------------------------------------------------------------
+def _oracle_chain_sweep(chain):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import dqmc as o
+    p = o.Params(W["Lx"], W["Ly"], W["t"], W["U"], W["beta"], W["dtau"], n_s=W["ns"])
+    ch = o.Chain(p, seed=0, chain=chain)
+    t0 = time.perf_counter()
+    out = ch.sweep(measure=True)
+    ch.gtau()
+    return time.perf_counter() - t0, out["accepted"]
+
+
+def _pool(workers):
+    import multiprocessing as mp
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"  # inherited by the spawned workers: one core each
+    return mp.get_context("spawn").Pool(workers)
+
+
+def oracle_step(pool, workers, first_chain):
+    t0 = time.perf_counter()
+    pool.map(_oracle_chain_sweep, range(first_chain, first_chain + workers))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(workers):
+    with _pool(workers) as pool:
+        wall = oracle_step(pool, workers, 0)
+    return {"value": updates_per_sweep(workers) / wall, "unit": UNIT, "cores": workers,
+            "kind": "oracle",
+            "sample": "%d chains of the workload, one full sweep each incl. G(tau), one "
+                      "single-threaded process per core, %.1f s wall" % (workers, wall)}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            self.p.wait(timeout=10)
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if len(r) > 5 + i and r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm.
+# ---------------------------------------------------------------------------
+def make_sim(pkg, precision, seed):
+    g = pkg.Group(Lx=W["Lx"], Ly=W["Ly"], t=W["t"], U=W["U"], beta=W["beta"], dtau=W["dtau"],
+                  n_chains=W["chains"], stab_interval=W["ns"], delay_k=W["k"], precision=precision)
+    return pkg.DQMC([g], seed=seed)
+
+
+def step_device(sim, gbuf):
+    sim.sweep(1, measure=True)
+    sim.gtau(out=gbuf)
+
+
+def time_arm(pkg, torch, precision, steps, warmup, seed, dist):
+    sim = make_sim(pkg, precision, seed)
+    gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        step_device(sim, gbuf)
+    sim.reset_stats()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = sim.launch_count()
+    with Clocks(torch.cuda.current_device()) as clk:
+        e0.record(st)
+        for _ in range(steps):
+            step_device(sim, gbuf)
+        e1.record(st)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    launches = sim.launch_count() - l0
+    drift, acc = sim.stats()
+    return sim, gbuf, {"ms": ms, "launches": launches, "drift": float(drift.max()),
+                       "acceptance": float(acc.sum()) / (updates_per_sweep(W["chains"]) * steps),
+                       "clocks": clk.summary()}
+
+
+def kernel_profile(sim, gbuf, steps, torch):
+    """Per-class device time (CUDA events around every launch) over `steps` sweeps."""
+    sim.timing(True)
+    sim.timing_reset()
+    for _ in range(steps):
+        step_device(sim, gbuf)
+    torch.cuda.synchronize()
+    t = sim.timing_read()
+    sim.timing(False)
+    return t
+
+
+def algorithmic_flops_per_sweep(cls, chains):
+    """FP64 flops per sweep of the FP64 linear-algebra classes (what the method
+    must compute, counted from the formulas, not from the kernels)."""
+    N, L, ns = n_sites(), n_slices(), W["ns"]
+    nc = -(-L // ns)
+    g = 2.0 * N ** 3
+    if cls == "gemm_f64":
+        # T updates (2 nc), recompute Mid + G (4 per point, nc points), G(tau) (6 per point, nc+1)
+        return chains * g * (2 * nc + 4 * nc + 6 * (nc + 1))
+    if cls == "qr_pivot":
+        # Householder R (4/3 N^3) + explicit Q (4/3 N^3), both stacks
+        return chains * 2 * nc * (8.0 / 3.0) * N ** 3
+    if cls == "gj_inverse":
+        return chains * (nc + (nc + 1)) * g
+    return None
+
+
+def roofline(profile, steps, peaks):
+    cls, (ms, n) = max(profile.items(), key=lambda kv: kv[1][0])
+    fl = algorithmic_flops_per_sweep(cls, W["chains"])
+    if fl is None or n == 0:
+        return {"bound": "latency", "kernel": cls, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+    per_launch = fl * steps / n
+    avg_s = ms / n / 1e3
+    ach = per_launch / avg_s / 1e12
+    peak = peaks["fp64_tflops"]
+    return {"bound": "alu", "kernel": cls, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+            "frac": ach / peak, "traffic": None, "peak_source": peaks["fp64_source"],
+            "flops_per_launch": per_launch, "avg_launch_ms": ms / n, "launches": n}
+
+
+def fp64_peak():
+    # FP64 issue rate from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
+    return {"fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+            "fp64_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz max SM clock"}
+
+
+def e2e_arm(pkg, torch, sim, steps):
+    """Same metric through the public API with host outputs: every step copies
+    G(k, tau) of all chains and the observables to host memory."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    nbytes = 0
+    for _ in range(steps):
+        sim.sweep(1, measure=True)
+        gt = sim.gtau()
+        ob = sim.observables()
+        nbytes = sum(a.nbytes for a in gt) + ob.nbytes
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": updates_per_sweep(W["chains"]) / dt, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "d2h_bytes_per_step": int(nbytes)}
+
+
+def run_ours(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_workers or min(os.cpu_count() or 1, 16))
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    seed = 1000 * rank  # independent chains per rank (weak scaling)
+
+    sim, gbuf, mixed = time_arm(pkg, torch, "fp32", args.steps, args.warmup, seed, dist)
+    prof = kernel_profile(sim, gbuf, args.steps, torch)
+    e2e = e2e_arm(pkg, torch, sim, max(1, min(args.steps, 3)))
+    sim.close()
+    sim64, gbuf64, plain = time_arm(pkg, torch, "fp64", args.steps, args.warmup, seed, dist)
+    sim64.close()
+
+    def slowest(ms):
+        if not dist:
+            return ms
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = slowest(mixed["ms"])
+    ms64 = slowest(plain["ms"])
+    value = world * updates_per_sweep(W["chains"]) / (ms / 1e3)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "fp32 Metropolis/delayed update/wrap, "
+                       "fp64 UDV/QR stabilisation, G recompute, drift, G(tau)",
+                       "chains_per_gpu": W["chains"], "L2": "working set > L2 (no flush needed)"},
+            "drift": mixed["drift"], "acceptance": mixed["acceptance"],
+            "fp64_plain": {"value": world * updates_per_sweep(W["chains"]) / (ms64 / 1e3),
+                           "ms_per_step": ms64, "drift": plain["drift"],
+                           "speedup_mixed_over_fp64": ms64 / ms},
+            "roofline": roofline(prof, args.steps, fp64_peak()),
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "e2e": e2e, "gpu_launches": mixed["launches"], "clocks": mixed["clocks"],
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    workers = args.cpu_workers or min(os.cpu_count() or 1, 16)
+    with _pool(workers) as pool:
+        chain = 0
+        for _ in range(args.warmup):
+            oracle_step(pool, workers, chain)
+            chain += workers
+        t = 0.0
+        for _ in range(args.steps):
+            t += oracle_step(pool, workers, chain)
+            chain += workers
+    ms = t / args.steps * 1e3
+    value = updates_per_sweep(workers) / (ms / 1e3)
+    sample = ("%d chains of the workload per step (one full oracle sweep incl. G(tau) per "
+              "single-threaded process)" % workers)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "oracle": "oracle/dqmc.py (numpy/scipy FP64)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-workers", type=int, default=0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * dqmc.h -- C ABI of the GB300 BSS determinant quantum Monte Carlo library
+ * (libdqmc.so) for the half-filled Hubbard model on periodic Lx x Ly square
+ * clusters, after Rost & Bluemer, arXiv:1504.05090, Sec. 2 "Model and
+ * Methods", Eqs. (1)-(3).
+ *
+ * Notation.  N = Lx*Ly sites, site i = x + Lx*y.  L = beta/dtau Trotter slices
+ * (the paper's Lambda, Eq. (2)).  K is the hopping matrix of Eq. (1)
+ * (K_ij = -t per nearest-neighbour bond and direction, periodic; a side of
+ * length 2 counts the +x and -x bond separately, so K_ij = -2t there).
+ * The Ising Hubbard-Stratonovich field s[l][i] = +-1 couples through
+ * V_l^sigma = sigma*lambda*diag(s_l) with cosh(lambda) = exp(dtau*U/2), and
+ * B_l^sigma = exp(-dtau K) exp(V_l^sigma); the weight of a field is
+ * det M_up det M_dn with M_sigma = I + B_L ... B_1 (Eq. (3)).
+ * G_sigma(l) = (I + B_l..B_1 B_L..B_{l+1})^{-1} is the equal-time Green
+ * function G_ij = <c_i c_j^dag>; G(l,0) = B_l .. B_1 G(0) the unequal-time one.
+ *
+ * Conventions for every entry point.
+ *  - Return 0 on success or a negative DQMC_ERR_* code; nothing throws or
+ *    aborts across this boundary.  dqmc_strerror() names a code.
+ *  - The context and all device state belong to the library and are freed by
+ *    dqmc_destroy().  Output buffers belong to the caller.
+ *  - Work is enqueued on the CUDA stream given to dqmc_init (NULL = the legacy
+ *    default stream).  Calls that write host memory synchronise that stream
+ *    before returning; calls with out_on_device != 0 do not.
+ *  - Chains are numbered globally in group order: group 0's chains first.
+ *    Arrays "per chain" are laid out in that order; a group's block of a
+ *    per-chain array with a group-dependent row length (field, G(tau)) has the
+ *    group's own length.
+ *  - The library needs a CUDA device of compute capability 10.3 (GB300) and
+ *    fails with DQMC_ERR_CUDA otherwise.  There is no CPU fallback.
+ */
+#ifndef DQMC_H
+#define DQMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define DQMC_OK 0
+#define DQMC_ERR_ARG (-1)     /* invalid argument (sizes, ranges, NULL)          */
+#define DQMC_ERR_CUDA (-2)    /* a CUDA runtime call or kernel launch failed     */
+#define DQMC_ERR_OOM (-3)     /* device allocation failed                        */
+#define DQMC_ERR_DRIFT (-4)   /* G drift above the context's drift limit         */
+#define DQMC_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up              */
+#define DQMC_ERR_NAN (-6)     /* a non-finite value appeared in G                */
+#define DQMC_ERR_STATE (-7)   /* call not valid in the context's current state   */
+
+/* Working precision of the Metropolis update, the delayed rank-k update and
+ * the slice wrap.  The QR/UDV stabilisation, the stabilised G recompute, the
+ * drift check, the unequal-time G at stabilisation points and all reported
+ * observables are FP64 in every mode. */
+#define DQMC_FP64 0
+#define DQMC_FP32 1
+
+/* Limits of this build. */
+#define DQMC_MAX_SIDE 16  /* Lx, Ly <= 16, so N <= 256                          */
+#define DQMC_MAX_DELAY 32 /* delay_k <= 32                                       */
+
+/* One group of chains with identical parameters (Eqs. (1)-(2)). */
+typedef struct {
+    int32_t Lx, Ly;        /* cluster sides; even, 2 <= Lx,Ly <= DQMC_MAX_SIDE.
+                              Even sides make the lattice bipartite, which the
+                              particle-hole evaluation of spin down requires. */
+    double t;              /* hopping, Eq. (1); the paper uses t = 0.25        */
+    double U;              /* interaction, Eq. (1); U >= 0                     */
+    double beta;           /* inverse temperature                              */
+    double dtau;           /* Trotter step; beta/dtau must be an integer to 1e-9 */
+    int32_t n_chains;      /* >= 1 independent Markov chains                   */
+    int32_t stab_interval; /* n_s >= 1: stabilise after every slice l with
+                              l % n_s == 0 and after l = L                      */
+    int32_t delay_k;       /* 1..DQMC_MAX_DELAY accepted flips per rank-k update */
+    int32_t precision;     /* DQMC_FP64 or DQMC_FP32                           */
+} dqmc_group;
+
+typedef struct dqmc_ctx dqmc_ctx; /* opaque, library-owned */
+
+/* Create a context: build exp(-+dtau K) (Eqs. (1)-(2)), draw each chain's
+ * initial field from Philox4x32-10 with key = seed (counter
+ * (i + N*l, 0xFFFFFFFF, chain, 1); s = +1 iff the first output word is odd),
+ * build the UDV stacks and the stabilised G(0) of every chain.
+ * groups: host array of n_groups >= 1 descriptors (copied).  stream: a
+ * cudaStream_t or NULL.  *out receives the context.  Errors: DQMC_ERR_ARG,
+ * DQMC_ERR_OOM, DQMC_ERR_CUDA.  Synchronises the stream. */
+int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed,
+              void* stream, dqmc_ctx** out);
+
+/* Run n_sweeps >= 0 Monte Carlo sweeps of every chain (Sec. 2: the sum of
+ * Eq. (3) sampled by Metropolis).  A sweep visits slices l = 1..L in order
+ * and sites i = 0..N-1 within a slice; the flip of s[l][i] is accepted iff
+ * u < R_up*R_dn, R_sigma = 1 + Delta_sigma (1 - G_sigma,ii),
+ * Delta_sigma = exp(-2 sigma lambda s) - 1, with u from Philox4x32-10
+ * (counter (i + N*(l-1), sweep, chain, 0), u = ((x0<<32|x1)>>11) 2^-53).
+ * Accepted flips update G by Sherman-Morrison, applied as delayed rank-k
+ * updates; G is wrapped to the next slice by B_l G B_l^{-1} and replaced by
+ * a freshly stabilised FP64 G after every stabilisation point, where the
+ * drift max|G_wrapped - G_fresh| / max|G_fresh| is recorded.  After the slice
+ * loop the left UDV stack is rebuilt for the new field.
+ * measure != 0: accumulate the equal-time observables (density, double
+ * occupancy, kinetic energy per site) at every stabilisation point.
+ * Enqueued asynchronously; errors of device-side checks surface at the next
+ * synchronising call.  Errors: DQMC_ERR_ARG, DQMC_ERR_CUDA. */
+int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure);
+
+/* Rebuild both UDV stacks of every chain from its current field and replace
+ * the working G by the stabilised G(0).  max_drift_out: host array [chains]
+ * receiving max|G_working - G_fresh| / max|G_fresh| before the replacement,
+ * or NULL.  Synchronises. */
+int dqmc_recompute_G(dqmc_ctx* ctx, double* max_drift_out);
+
+/* Unequal-time Green function of the current field of every chain (Sec. 2,
+ * "Green functions G_ij(tau_l) on a discrete imaginary-time grid"):
+ * out[chain][l][k] = 1/2 sum_sigma Re G_sigma,k(tau_l), l = 0..L, where
+ * G_k = (1/N) sum_ij cos(k.(r_i - r_j)) G_ij(l,0), k = 2 pi (kx/Lx, ky/Ly)
+ * with index kx + Lx*ky.  G(l,0) is formed stably at every stabilisation
+ * point and propagated by B_l in between.  Row length per chain is
+ * (L_g + 1) * N_g of its group; dqmc_gtau_size() gives the total.
+ * out: caller-owned doubles, on the device if out_on_device else on the host.
+ * Requires current UDV stacks (true after dqmc_init, dqmc_sweep,
+ * dqmc_set_field and dqmc_recompute_G). */
+int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device);
+int64_t dqmc_gtau_size(const dqmc_ctx* ctx);
+
+/* Derivatives of log W = log|det M_up| + log|det M_dn| (Eq. (3)) of the
+ * current field of every chain, with respect to the hopping t (lambda and
+ * the field fixed) and to the HS coupling lambda (t fixed):
+ *   dlogW/dt      = dtau sum_sigma sum_l tr[A (I - G_sigma(l))], K = -t A,
+ *   dlogW/dlambda = sum_sigma sigma sum_{l,i} s_li (1 - G_sigma,ii(l-1)),
+ * and log W itself.  Each output: per-chain doubles or NULL, on the device if
+ * out_on_device else on the host. */
+int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda,
+              double* logW, int out_on_device);
+
+/* Copy all fields out (int8 [chain][L_g][N_g], host) / in.  dqmc_set_field
+ * rebuilds the stacks and G(0) of every chain; values must be +-1. */
+int dqmc_get_field(const dqmc_ctx* ctx, int8_t* out);
+int dqmc_set_field(dqmc_ctx* ctx, const int8_t* in);
+int64_t dqmc_field_size(const dqmc_ctx* ctx);
+
+/* Stabilised FP64 G(0) of one chain and spin (0 = up, 1 = down) into a host
+ * N*N row-major array.  Spin down is I - P G_up^T P, P = diag((-1)^(x+y)). */
+int dqmc_get_G(const dqmc_ctx* ctx, int chain, int spin, double* out);
+
+/* Accumulated equal-time observables, host [chain][4]:
+ * sum of density, sum of double occupancy, sum of kinetic energy per site,
+ * number of measurements.  dqmc_reset_observables zeroes them. */
+int dqmc_get_observables(const dqmc_ctx* ctx, double* out);
+int dqmc_reset_observables(dqmc_ctx* ctx);
+
+/* Per-chain statistics since the last reset: maximum G drift seen at a
+ * stabilisation point (host doubles [chain]) and accepted flips (host
+ * uint64 [chain]); either pointer may be NULL. */
+int dqmc_get_stats(const dqmc_ctx* ctx, double* max_drift, uint64_t* accepted);
+int dqmc_reset_stats(dqmc_ctx* ctx);
+
+/* Total number of chains in the context. */
+int dqmc_num_chains(const dqmc_ctx* ctx);
+
+/* Number of kernel launches the library enqueued since the context was
+ * created (for launch accounting). */
+int64_t dqmc_launch_count(const dqmc_ctx* ctx);
+
+/* Optional per-launch timing (library tracing).  While enabled, every kernel
+ * launch is bracketed by a pair of CUDA events on the context's stream and its
+ * device time is added to the class of the kernel (metropolis, wrap,
+ * stack_kron, qr_pivot, gemm_f64, gj_inverse, gtau_propagate, gtau_finalize,
+ * grad_terms, misc).  dqmc_timing_read synchronises, writes up to n_classes
+ * summed milliseconds and launch counts (either pointer may be NULL) and
+ * returns the number of classes; dqmc_timing_class_name names a class. */
+int dqmc_timing_enable(dqmc_ctx* ctx, int on);
+int dqmc_timing_read(dqmc_ctx* ctx, double* ms, int64_t* launches, int n_classes);
+int dqmc_timing_reset(dqmc_ctx* ctx);
+const char* dqmc_timing_class_name(int cls);
+
+void dqmc_destroy(dqmc_ctx* ctx);
+const char* dqmc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DQMC_H */

@@ -1,0 +1,241 @@
+"""GB300 BSS determinant QMC for the half-filled 2D Hubbard model.
+
+Python binding of libdqmc (include/dqmc.h): argument marshalling around the
+CUDA library, plus `LogWeight`, a torch.autograd.Function whose backward is
+the library's adjoint of log det(I + B_L ... B_1).  Model and notation follow
+Rost & Bluemer, arXiv:1504.05090, Sec. 2, Eqs. (1)-(3).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+
+__all__ = ["Group", "DQMC", "LogWeight", "DqmcError", "n_slices"]
+
+DqmcError = _lib.DqmcError
+_LIB = None
+
+
+def lib():
+    """The loaded libdqmc (raises ImportError if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        _LIB = _lib.load()
+    return _LIB
+
+
+def n_slices(beta, dtau):
+    return int(round(beta / dtau))
+
+
+@dataclass
+class Group:
+    """One group of identical chains: cluster Lx x Ly, Eq. (1) parameters t, U,
+    inverse temperature beta, Trotter step dtau (Eq. (2)), n_chains chains,
+    stabilisation interval n_s, delay depth k and working precision."""
+    Lx: int
+    Ly: int
+    t: float = 0.25
+    U: float = 2.0
+    beta: float = 2.0
+    dtau: float = 0.125
+    n_chains: int = 1
+    stab_interval: int = 10
+    delay_k: int = 16
+    precision: str = "fp64"
+
+    @property
+    def N(self):
+        return self.Lx * self.Ly
+
+    @property
+    def L(self):
+        return n_slices(self.beta, self.dtau)
+
+    def _c(self):
+        prec = {"fp64": _lib.DQMC_FP64, "fp32": _lib.DQMC_FP32}[self.precision]
+        return _lib.DqmcGroup(self.Lx, self.Ly, self.t, self.U, self.beta, self.dtau,
+                              self.n_chains, self.stab_interval, self.delay_k, prec)
+
+
+def _ptr(a):
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class DQMC:
+    """A context of Markov chains living on the current CUDA device.
+
+    All work is enqueued on the torch stream current at construction."""
+
+    def __init__(self, groups, seed=0, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("DQMC needs a CUDA device")
+        self.groups = list(groups)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        arr = (_lib.DqmcGroup * len(self.groups))(*[g._c() for g in self.groups])
+        h = ctypes.c_void_p()
+        _lib.check(lib().dqmc_init(arr, len(self.groups), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                   ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
+                   "dqmc_init")
+        self._h = h
+        self.n_chains = lib().dqmc_num_chains(h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dqmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- Monte Carlo --------------------------------------------------------
+    def sweep(self, n=1, measure=True):
+        _lib.check(lib().dqmc_sweep(self._h, int(n), int(bool(measure))), "dqmc_sweep")
+
+    def recompute_G(self):
+        out = np.zeros(self.n_chains)
+        _lib.check(lib().dqmc_recompute_G(self._h, _ptr(out)), "dqmc_recompute_G")
+        return out
+
+    # -- state --------------------------------------------------------------
+    def field(self):
+        out = np.empty(lib().dqmc_field_size(self._h), dtype=np.int8)
+        _lib.check(lib().dqmc_get_field(self._h, _ptr(out)), "dqmc_get_field")
+        return self._split(out, lambda g: (g.n_chains, g.L, g.N))
+
+    def set_field(self, fields):
+        flat = np.concatenate([np.ascontiguousarray(f, dtype=np.int8).ravel() for f in fields])
+        _lib.check(lib().dqmc_set_field(self._h, _ptr(flat)), "dqmc_set_field")
+
+    def G(self, chain, spin=0):
+        g = self._group_of(chain)
+        out = np.empty((g.N, g.N))
+        _lib.check(lib().dqmc_get_G(self._h, int(chain), int(spin), _ptr(out)), "dqmc_get_G")
+        return out
+
+    def observables(self):
+        out = np.empty((self.n_chains, 4))
+        _lib.check(lib().dqmc_get_observables(self._h, _ptr(out)), "dqmc_get_observables")
+        return out
+
+    def reset_observables(self):
+        _lib.check(lib().dqmc_reset_observables(self._h), "dqmc_reset_observables")
+
+    def stats(self):
+        drift = np.empty(self.n_chains)
+        acc = np.empty(self.n_chains, dtype=np.uint64)
+        _lib.check(lib().dqmc_get_stats(self._h, _ptr(drift), _ptr(acc)), "dqmc_get_stats")
+        return drift, acc
+
+    def reset_stats(self):
+        _lib.check(lib().dqmc_reset_stats(self._h), "dqmc_reset_stats")
+
+    def launch_count(self):
+        return int(lib().dqmc_launch_count(self._h))
+
+    def timing(self, on=True):
+        """Enable/disable per-launch CUDA-event timing by kernel class."""
+        _lib.check(lib().dqmc_timing_enable(self._h, int(bool(on))), "dqmc_timing_enable")
+
+    def timing_reset(self):
+        _lib.check(lib().dqmc_timing_reset(self._h), "dqmc_timing_reset")
+
+    def timing_read(self):
+        """{class name: (total ms, launches)} since the last reset."""
+        ms = np.zeros(16)
+        n = np.zeros(16, dtype=np.int64)
+        k = _lib.check(lib().dqmc_timing_read(self._h, _ptr(ms), _ptr(n), 16), "dqmc_timing_read")
+        return {lib().dqmc_timing_class_name(c).decode(): (float(ms[c]), int(n[c]))
+                for c in range(k)}
+
+    # -- measurements -------------------------------------------------------
+    def gtau(self, out=None):
+        """Spin-averaged Re G_k(tau_l) per chain: a list (per group) of arrays
+        [chains, L+1, N]; with `out` (a CUDA float64 tensor of
+        dqmc_gtau_size elements) the result stays on the device."""
+        n = int(lib().dqmc_gtau_size(self._h))
+        if out is not None:
+            assert out.is_cuda and out.numel() == n
+            _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(out), 1), "dqmc_measure_Gtau")
+            return out
+        host = np.empty(n)
+        _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(host), 0), "dqmc_measure_Gtau")
+        return self._split(host, lambda g: (g.n_chains, g.L + 1, g.N))
+
+    def grad(self):
+        """(dlogW/dt, dlogW/dlambda, logW) per chain, host arrays."""
+        dt = np.empty(self.n_chains)
+        dl = np.empty(self.n_chains)
+        lw = np.empty(self.n_chains)
+        _lib.check(lib().dqmc_grad(self._h, _ptr(dt), _ptr(dl), _ptr(lw), 0), "dqmc_grad")
+        return dt, dl, lw
+
+    def grad_device(self, dt, dl, lw):
+        _lib.check(lib().dqmc_grad(self._h, _ptr(dt), _ptr(dl), _ptr(lw), 1), "dqmc_grad")
+
+    # -- helpers ------------------------------------------------------------
+    def _group_of(self, chain):
+        c = 0
+        for g in self.groups:
+            if chain < c + g.n_chains:
+                return g
+            c += g.n_chains
+        raise IndexError(chain)
+
+    def _split(self, flat, shape_of):
+        out, off = [], 0
+        for g in self.groups:
+            shp = shape_of(g)
+            n = int(np.prod(shp))
+            out.append(flat[off:off + n].reshape(shp))
+            off += n
+        return out
+
+
+class LogWeight:
+    """torch.autograd.Function: log W = log|det M_up| + log|det M_dn| of the
+    current field of every chain as a function of (t, lambda).  The forward
+    value and both derivatives come from one dqmc_grad call; backward returns
+    sum_c grad_out[c] * dlogW_c/dt and the same for lambda.  The inputs must
+    equal the parameters the context was built with (the field and the
+    B matrices are not re-derived from them)."""
+
+    @staticmethod
+    def apply(sim: DQMC, t, lam):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, t_, lam_):
+                dev = torch.device("cuda")
+                dt = torch.empty(sim.n_chains, dtype=torch.float64, device=dev)
+                dl = torch.empty_like(dt)
+                lw = torch.empty_like(dt)
+                sim.grad_device(dt, dl, lw)
+                ctx.save_for_backward(dt, dl)
+                return lw
+
+            @staticmethod
+            def backward(ctx, gout):
+                dt, dl = ctx.saved_tensors
+                return (gout * dt).sum().to(t.dtype), (gout * dl).sum().to(lam.dtype)
+
+        return _Fn.apply(t, lam)

@@ -1,0 +1,74 @@
+// Shared device helpers of libdqmc: Philox4x32-10, lattice geometry, the
+// argument blocks passed by value to the kernels, and launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace dqmc {
+
+constexpr int kMaxSide = 16;
+constexpr int kMaxN = kMaxSide * kMaxSide;  // 256 sites
+constexpr int kMaxDelay = 32;
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of the
+// multiply-xor bijection with a Weyl-sequence key schedule.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Uniform double in [0, 1) from the top 53 of the 64 bits (x0:x1).
+__device__ __forceinline__ double uniform53(uint32_t x0, uint32_t x1) {
+  const uint64_t b = ((static_cast<uint64_t>(x0) << 32) | x1) >> 11;
+  return static_cast<double>(b) * 0x1.0p-53;
+}
+
+// Counter tags of the two random streams.
+constexpr uint32_t kTagProposal = 0u;
+constexpr uint32_t kTagInitField = 1u;
+
+// ---------------------------------------------------------------------------
+// Geometry: site i = x + Lx*y on a periodic Lx x Ly cluster.
+// ---------------------------------------------------------------------------
+struct Geom {
+  int Lx, Ly, N;
+};
+
+// Site index of (i shifted by -r) used by the separation bins r = r_i - r_j.
+__device__ __forceinline__ int sep_index(int i, int j, const Geom& g) {
+  const int xi = i % g.Lx, yi = i / g.Lx, xj = j % g.Lx, yj = j / g.Lx;
+  const int rx = (xi - xj + g.Lx) % g.Lx, ry = (yi - yj + g.Ly) % g.Ly;
+  return rx + g.Lx * ry;
+}
+
+// ---------------------------------------------------------------------------
+// Kronecker application of exp(-+dtau K) = Ey (x) Ex to vectors of length N,
+// optionally combined with the diagonal exp(+-sigma lambda s_l).  Ex and Ey
+// are circulant: Ex[x][x'] = ex[(x - x') mod Lx].  Kinds:
+//   kB   : v <- E  (e^{+c s_l} o v)     = B_l v          (c = sigma lambda)
+//   kBT  : v <- e^{+c s_l} o (E v)      = B_l^T v
+//   kBIT : v <- E^{-1} (e^{-c s_l} o v) = B_l^{-T} v
+// ---------------------------------------------------------------------------
+enum KronKind : int { kB = 0, kBT = 1, kBIT = 2 };
+
+struct KronTaps {
+  double ex[kMaxSide], ey[kMaxSide];    // circulant taps of exp(-dtau K_x), exp(-dtau K_y)
+  double exi[kMaxSide], eyi[kMaxSide];  // taps of the inverses
+};
+
+// Error/status word written by device code (never trapped).
+enum DevStatus : int { kDevOk = 0, kDevBadArg = 1, kDevNonFinite = 2, kDevSingular = 3 };
+
+}  // namespace dqmc

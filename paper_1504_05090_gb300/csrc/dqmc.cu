@@ -1,0 +1,901 @@
+// Host runtime and C ABI of libdqmc (see include/dqmc.h).
+//
+// One context holds groups of independent Markov chains.  Device state per
+// group (FP64 unless noted, chains batch-major):
+//   field  int8 [C][L][N]           Ising HS field (Sec. 2)
+//   Gw     T    [C][N][N]           working G(l) of spin up (T = double/float)
+//   G64         [C][N][N]           last stabilised G
+//   RU,RT       [C][nc+1][N][N]     right stack R_c = B_c..B_1 = U D T (U stored transposed)
+//   RD          [C][nc+1][N]
+//   LU,LT,LD                        left stack, UDT factors of L_c^T = (B_L..B_{c+1})^T
+//   X,Rtil      [C][N][N]           QR workspace
+//   Mid,W1,W2,A1,A2 [C][nc+1][N][N] stabilised-G workspaces (all stabilisation points at once)
+// Stabilisation points cp[j] = min(j n_s, L), j = 0..nc.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dqmc.h"
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dqmc {
+
+__global__ void k_increment(uint32_t* ctr) { *ctr += 1u; }
+
+__global__ void k_zero(double* p, long long n) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x)
+    p[e] = 0.0;
+}
+
+// log W = 2 (sum log Db_L(0) + log|det Mid(0)|) - lambda sum_il s_il   (det M_dn = e^{-lambda sum s} det M_up)
+__global__ void k_logw(const double* LD0, long long sLD, const double* logabs_mid, long long sMid,
+                       const int8_t* field, int L, int N, double lam, double* out) {
+  const int c = blockIdx.x;
+  double a = 0.0, s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += log(fmax(LD0[c * sLD + i], 1.0));
+  for (long long e = threadIdx.x; e < static_cast<long long>(L) * N; e += blockDim.x)
+    s += field[static_cast<size_t>(c) * L * N + e];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+    s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  }
+  __shared__ double sa[32], ss[32];
+  if ((threadIdx.x & 31) == 0) {
+    sa[threadIdx.x >> 5] = a;
+    ss[threadIdx.x >> 5] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      a += sa[w];
+      s += ss[w];
+    }
+    out[c] = 2.0 * (a + logabs_mid[c * sMid]) - lam * s;
+  }
+}
+
+__global__ void k_pick3(const double* acc, double* dt, double* dl, int C) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    if (dt) dt[c] = acc[c * 3 + 0];
+    if (dl) dl[c] = acc[c * 3 + 1];
+  }
+}
+
+struct Group {
+  dqmc_group p;
+  int N = 0, L = 0, nc = 0, C = 0, chain0 = 0;
+  double lam = 0.0;
+  std::vector<int> cp;
+  KronTaps taps{};
+  int8_t* field = nullptr;
+  void* Gw = nullptr;
+  double *G64 = nullptr, *RU = nullptr, *RD = nullptr, *RT = nullptr;
+  double *LU = nullptr, *LD = nullptr, *LT = nullptr;
+  double *X = nullptr, *Rtil = nullptr;
+  double *Mid = nullptr, *W1 = nullptr, *W2 = nullptr, *A1 = nullptr, *A2 = nullptr;
+  double *logabs = nullptr, *obs = nullptr, *drift = nullptr, *bins = nullptr, *gacc = nullptr;
+  double* gout = nullptr;  // [C][L+1][N] staging of G(tau) for host output
+  unsigned long long* acc = nullptr;
+  int *d_cp_gtau = nullptr, *d_cp_grad = nullptr;
+  long long nn() const { return static_cast<long long>(N) * N; }
+  long long sstride() const { return static_cast<long long>(nc + 1) * N * N; }
+};
+
+}  // namespace dqmc
+
+using namespace dqmc;
+
+// Kernel classes for the optional per-launch timing (dqmc_timing_*).
+enum TimingClass : int {
+  kTMetropolis = 0, kTWrap, kTStackKron, kTQR, kTGemm, kTInverse, kTGtauProp, kTGtauFinal,
+  kTGrad, kTMisc, kTNumClasses
+};
+static const char* kTimingNames[kTNumClasses] = {
+    "metropolis", "wrap", "stack_kron", "qr_pivot", "gemm_f64", "gj_inverse", "gtau_propagate",
+    "gtau_finalize", "grad_terms", "misc"};
+
+struct dqmc_ctx {
+  std::vector<Group> g;
+  cudaStream_t st = nullptr;
+  // timing: event pairs recorded around launches while enabled
+  bool timing = false;
+  int tclass = kTMisc;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_class;
+  size_t ev_used = 0;
+  double tms[kTNumClasses] = {};
+  long long tcount[kTNumClasses] = {};
+  uint64_t seed = 0;
+  uint32_t* d_sweep = nullptr;
+  int* d_status = nullptr;
+  int total = 0;
+  long long launches = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+#define DQ_CK(call)                                 \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return DQMC_ERR_CUDA;    \
+  } while (0)
+#define DQ_RET(call)                 \
+  do {                               \
+    int r_ = (call);                 \
+    if (r_ != DQMC_OK) return r_;    \
+  } while (0)
+#define DQ_LAUNCH(ctx, call)                        \
+  do {                                              \
+    ++(ctx)->launches;                              \
+    const int slot_ = timing_begin(ctx);            \
+    DQ_CK(call);                                    \
+    if (slot_ >= 0) DQ_CK(timing_end(ctx, slot_));  \
+  } while (0)
+int timing_begin(dqmc_ctx* ctx);
+cudaError_t timing_end(dqmc_ctx* ctx, int slot);
+#define DQ_CLASS(ctx, c) ((ctx)->tclass = (c))
+#define DQ_LAUNCH_C(ctx, c, call) \
+  do {                            \
+    DQ_CLASS(ctx, c);             \
+    DQ_LAUNCH(ctx, call);         \
+  } while (0)
+
+// Fold the elapsed times of all recorded pairs into the per-class sums.
+int timing_fold(dqmc_ctx* ctx) {
+  if (ctx->ev_used == 0) return DQMC_OK;
+  DQ_CK(cudaEventSynchronize(ctx->ev[2 * (ctx->ev_used - 1) + 1]));
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0.f;
+    DQ_CK(cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    ctx->tms[ctx->ev_class[i]] += ms;
+    ctx->tcount[ctx->ev_class[i]] += 1;
+  }
+  ctx->ev_used = 0;
+  return DQMC_OK;
+}
+
+int timing_begin(dqmc_ctx* ctx) {
+  if (!ctx->timing) return -1;
+  if (ctx->ev_used * 2 >= ctx->ev.size()) {
+    if (timing_fold(ctx) != DQMC_OK) return -1;
+  }
+  const size_t slot = ctx->ev_used++;
+  ctx->ev_class[slot] = ctx->tclass;
+  if (cudaEventRecord(ctx->ev[2 * slot], ctx->st) != cudaSuccess) return -1;
+  return static_cast<int>(slot);
+}
+
+cudaError_t timing_end(dqmc_ctx* ctx, int slot) {
+  return cudaEventRecord(ctx->ev[2 * slot + 1], ctx->st);
+}
+
+template <typename P>
+int dev_alloc(dqmc_ctx* ctx, P** p, size_t bytes) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    return DQMC_ERR_OOM;
+  }
+  ctx->allocs.push_back(q);
+  *p = static_cast<P*>(q);
+  return DQMC_OK;
+}
+
+// Circulant taps of exp(-+dtau K_1D) on a periodic ring of length n with
+// one-dimensional band -2t cos k: e[d] = (1/n) sum_m cos(2 pi m d / n) exp(+-2 t dtau cos(2 pi m / n)).
+void ring_taps(int n, double t, double dtau, double* e, double* ei) {
+  for (int d = 0; d < kMaxSide; ++d) {
+    e[d] = 0.0;
+    ei[d] = 0.0;
+  }
+  for (int d = 0; d < n; ++d) {
+    double a = 0.0, b = 0.0;
+    for (int m = 0; m < n; ++m) {
+      const double k = 2.0 * M_PI * m / n;
+      const double c = std::cos(k * d);
+      a += c * std::exp(2.0 * t * dtau * std::cos(k));
+      b += c * std::exp(-2.0 * t * dtau * std::cos(k));
+    }
+    e[d] = a / n;
+    ei[d] = b / n;
+  }
+}
+
+KronArgs kron_base(const Group& g, int kind, int nv) {
+  KronArgs a{};
+  a.N = g.N;
+  a.Lx = g.p.Lx;
+  a.Ly = g.p.Ly;
+  a.L = g.L;
+  a.nv = nv;
+  a.kind = kind;
+  a.c = g.lam;  // sigma = +1 (spin up)
+  a.taps = g.taps;
+  a.field = g.field;
+  a.mat_stride = g.nn();
+  a.out_stride = g.nn();
+  a.per_chain = 1;
+  a.dir = 1;
+  return a;
+}
+
+int kron_nv(const Group& g, bool fp64) {
+  // vectors per CTA: as many as fit comfortably in shared memory
+  const int budget = fp64 ? 120 * 1024 : 110 * 1024;
+  const int per = (g.N + 1) * 2 * (fp64 ? 8 : 4);
+  int nv = std::max(1, std::min(32, budget / per));
+  return std::min(nv, g.N);
+}
+
+GemmArgs gemm0(int n) {
+  GemmArgs a{};
+  a.n = n;
+  a.alpha = 1.0;
+  return a;
+}
+
+// ---- UDV stack steps ------------------------------------------------------
+
+// Right stack entry j from entry j-1 and slices cp[j-1]+1 .. cp[j].
+int stack_right(dqmc_ctx* ctx, Group& g, int j) {
+  KronArgs a = kron_base(g, kB, kron_nv(g, true));
+  a.mat_stride = g.sstride();
+  a.out_stride = g.nn();
+  a.vscale = g.RD + static_cast<long long>(j - 1) * g.N;
+  a.vscale_stride = static_cast<long long>(g.nc + 1) * g.N;
+  a.l0_first = g.cp[j - 1];
+  a.dir = 1;
+  a.n_slices = g.cp[j] - g.cp[j - 1];
+  DQ_CLASS(ctx, kTStackKron);
+  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.RU + (j - 1) * g.nn(), g.X, g.C, a, ctx->st));
+  DQ_CLASS(ctx, kTQR);
+  DQ_LAUNCH(ctx, launch_qrp(g.X, g.nn(), g.RU + j * g.nn(), g.sstride(), g.RD + j * g.N,
+                            static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.N, g.C,
+                            ctx->d_status, ctx->st));
+  GemmArgs m = gemm0(g.N);
+  m.A = g.Rtil; m.sA = g.nn();
+  m.B = g.RT + (j - 1) * g.nn(); m.sB = g.sstride();
+  m.C = g.RT + j * g.nn(); m.sC = g.sstride();
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  return DQMC_OK;
+}
+
+// Left stack entry j from entry j+1 and slices cp[j+1] .. cp[j]+1 (descending).
+int stack_left(dqmc_ctx* ctx, Group& g, int j) {
+  KronArgs a = kron_base(g, kBT, kron_nv(g, true));
+  a.mat_stride = g.sstride();
+  a.out_stride = g.nn();
+  a.vscale = g.LD + static_cast<long long>(j + 1) * g.N;
+  a.vscale_stride = static_cast<long long>(g.nc + 1) * g.N;
+  a.l0_first = g.cp[j + 1] - 1;
+  a.dir = -1;
+  a.n_slices = g.cp[j + 1] - g.cp[j];
+  DQ_CLASS(ctx, kTStackKron);
+  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.LU + (j + 1) * g.nn(), g.X, g.C, a, ctx->st));
+  DQ_CLASS(ctx, kTQR);
+  DQ_LAUNCH(ctx, launch_qrp(g.X, g.nn(), g.LU + j * g.nn(), g.sstride(), g.LD + j * g.N,
+                            static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.N, g.C,
+                            ctx->d_status, ctx->st));
+  GemmArgs m = gemm0(g.N);
+  m.A = g.Rtil; m.sA = g.nn();
+  m.B = g.LT + (j + 1) * g.nn(); m.sB = g.sstride();
+  m.C = g.LT + j * g.nn(); m.sC = g.sstride();
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  return DQMC_OK;
+}
+
+// Mid = Db_R^{-1} (U_R^T U_L) Db_L^{-1} + Ds_R (T_R T_L^T) Ds_L for `batch`
+// stack entries starting at entry j0 of every chain (stride `es` between the
+// entries of one batch), written to out (stride N^2).
+int form_mid(dqmc_ctx* ctx, Group& g, int j0, long long es, int batch, double* out) {
+  const long long dstride = es / g.N;  // D vectors have stride es/N
+  GemmArgs m = gemm0(g.N);
+  m.A = g.RU + j0 * g.nn(); m.sA = es; m.tA = 0;
+  m.B = g.LU + j0 * g.nn(); m.sB = es; m.tB = 1;
+  m.C = out; m.sC = g.nn();
+  m.rs = g.RD + j0 * g.N; m.srs = dstride; m.rs_mode = 2;
+  m.cs = g.LD + j0 * g.N; m.scs = dstride; m.cs_mode = 2;
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+  m.A = g.RT + j0 * g.nn();
+  m.B = g.LT + j0 * g.nn();
+  m.rs_mode = 3;
+  m.cs_mode = 3;
+  m.beta = 1.0;
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+  return DQMC_OK;
+}
+
+// G64 = U_L Db_L^{-1} Mid^{-1} Db_R^{-1} U_R^T at stack entry j of every chain.
+int recompute(dqmc_ctx* ctx, Group& g, int j) {
+  DQ_RET(form_mid(ctx, g, j, g.sstride(), g.C, g.X));
+  DQ_CLASS(ctx, kTInverse);
+  DQ_LAUNCH(ctx, launch_gj_inverse(g.X, g.nn(), g.N, g.C, nullptr, nullptr, ctx->d_status, ctx->st));
+  GemmArgs m = gemm0(g.N);
+  m.A = g.LU + j * g.nn(); m.sA = g.sstride(); m.tA = 1;
+  m.ks = g.LD + j * g.N; m.sks = static_cast<long long>(g.nc + 1) * g.N; m.ks_mode = 2;
+  m.B = g.X; m.sB = g.nn();
+  m.C = g.Rtil; m.sC = g.nn();
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  m = gemm0(g.N);
+  m.A = g.Rtil; m.sA = g.nn();
+  m.ks = g.RD + j * g.N; m.sks = static_cast<long long>(g.nc + 1) * g.N; m.ks_mode = 2;
+  m.B = g.RU + j * g.nn(); m.sB = g.sstride();
+  m.C = g.G64; m.sC = g.nn();
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  return DQMC_OK;
+}
+
+template <typename T>
+int drift_reset(dqmc_ctx* ctx, Group& g) {
+  DQ_CLASS(ctx, kTMisc);
+  DQ_LAUNCH(ctx, launch_drift_reset<T>(g.G64, static_cast<T*>(g.Gw), g.C, g.N, g.drift,
+                                        ctx->d_status, ctx->st));
+  return DQMC_OK;
+}
+
+int drift_reset_any(dqmc_ctx* ctx, Group& g) {
+  return g.p.precision == DQMC_FP32 ? drift_reset<float>(ctx, g) : drift_reset<double>(ctx, g);
+}
+
+int left_pass(dqmc_ctx* ctx, Group& g) {
+  for (int j = g.nc - 1; j >= 0; --j) DQ_RET(stack_left(ctx, g, j));
+  return DQMC_OK;
+}
+
+int right_pass(dqmc_ctx* ctx, Group& g) {
+  for (int j = 1; j <= g.nc; ++j) DQ_RET(stack_right(ctx, g, j));
+  return DQMC_OK;
+}
+
+// Both stacks from the current field and the stabilised G(0); the working G
+// is overwritten (its drift against G(0) is recorded when record != 0).
+int rebuild(dqmc_ctx* ctx, Group& g) {
+  DQ_CLASS(ctx, kTMisc);
+  DQ_LAUNCH(ctx, launch_set_identity(g.RU, g.sstride(), g.RD, static_cast<long long>(g.nc + 1) * g.N,
+                                     g.N, g.C, ctx->st));
+  DQ_CLASS(ctx, kTMisc);
+  DQ_LAUNCH(ctx, launch_set_identity(g.RT, g.sstride(), nullptr, 0, g.N, g.C, ctx->st));
+  DQ_CLASS(ctx, kTMisc);
+  DQ_LAUNCH(ctx, launch_set_identity(g.LU + g.nc * g.nn(), g.sstride(), g.LD + g.nc * g.N,
+                                     static_cast<long long>(g.nc + 1) * g.N, g.N, g.C, ctx->st));
+  DQ_CLASS(ctx, kTMisc);
+  DQ_LAUNCH(ctx, launch_set_identity(g.LT + g.nc * g.nn(), g.sstride(), nullptr, 0, g.N, g.C,
+                                     ctx->st));
+  DQ_RET(right_pass(ctx, g));
+  DQ_RET(left_pass(ctx, g));
+  DQ_RET(recompute(ctx, g, 0));
+  return DQMC_OK;
+}
+
+template <typename T>
+int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
+  const double em2 = std::expm1(-2.0 * g.lam), ep2 = std::expm1(2.0 * g.lam);
+  MetroArgs ma{};
+  ma.N = g.N;
+  ma.L = g.L;
+  ma.k = g.p.delay_k;
+  ma.chain0 = g.chain0;
+  ma.key0 = static_cast<uint32_t>(ctx->seed);
+  ma.key1 = static_cast<uint32_t>(ctx->seed >> 32);
+  ma.sweep_ctr = ctx->d_sweep;
+  ma.em2 = em2;
+  ma.ep2 = ep2;
+  ma.accepted = g.acc;
+  const bool fp64 = sizeof(T) == 8;
+  KronArgs wl = kron_base(g, kB, kron_nv(g, fp64));
+  KronArgs wr = kron_base(g, kBIT, kron_nv(g, fp64));
+  wl.n_slices = wr.n_slices = 1;
+  T* Gw = static_cast<T*>(g.Gw);
+  int j = 1;
+  for (int l = 1; l <= g.L; ++l) {
+    ma.l0 = l - 1;
+    DQ_CLASS(ctx, kTMetropolis);
+    DQ_LAUNCH(ctx, launch_metropolis<T>(Gw, g.field, g.C, ma, ctx->st));
+    wl.l0_first = wr.l0_first = l - 1;
+    DQ_CLASS(ctx, kTWrap);
+    DQ_LAUNCH(ctx, launch_kron_cols<T>(Gw, g.C, wl, ctx->st));
+    DQ_CLASS(ctx, kTWrap);
+    DQ_LAUNCH(ctx, launch_kron_rows<T>(Gw, Gw, g.C, wr, ctx->st));
+    if (l == g.cp[j]) {
+      DQ_RET(stack_right(ctx, g, j));
+      DQ_RET(recompute(ctx, g, j));
+      DQ_RET(drift_reset<T>(ctx, g));
+      if (measure)
+        DQ_LAUNCH_C(ctx, kTMisc, launch_observables(g.G64, g.C, g.p.Lx, g.p.Ly, g.p.t, g.obs, ctx->st));
+      ++j;
+    }
+  }
+  return DQMC_OK;
+}
+
+int sweep_group(dqmc_ctx* ctx, Group& g, int measure) {
+  if (g.p.precision == DQMC_FP32)
+    DQ_RET(up_pass<float>(ctx, g, measure));
+  else
+    DQ_RET(up_pass<double>(ctx, g, measure));
+  return left_pass(ctx, g);
+}
+
+int check_status(dqmc_ctx* ctx) {
+  DQ_CK(cudaStreamSynchronize(ctx->st));
+  int s = 0;
+  DQ_CK(cudaMemcpy(&s, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (s == kDevNonFinite) return DQMC_ERR_NAN;
+  if (s != 0) return DQMC_ERR_NAN;
+  return DQMC_OK;
+}
+
+// Stabilised matrices at all stabilisation points of every chain:
+// Mid^{-1} in g.Mid and W1 = U_L Db_L^{-1} Mid^{-1} in g.W1.
+int all_points_w1(dqmc_ctx* ctx, Group& g) {
+  const int batch = g.C * (g.nc + 1);
+  DQ_RET(form_mid(ctx, g, 0, g.nn(), batch, g.Mid));
+  DQ_CLASS(ctx, kTInverse);
+  DQ_LAUNCH(ctx, launch_gj_inverse(g.Mid, g.nn(), g.N, batch, g.logabs, nullptr, ctx->d_status,
+                                   ctx->st));
+  GemmArgs m = gemm0(g.N);
+  m.A = g.LU; m.sA = g.nn(); m.tA = 1;
+  m.ks = g.LD; m.sks = g.N; m.ks_mode = 2;
+  m.B = g.Mid; m.sB = g.nn();
+  m.C = g.W1; m.sC = g.nn();
+  DQ_CLASS(ctx, kTGemm);
+  DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+  return DQMC_OK;
+}
+
+int validate(const dqmc_group& p) {
+  if (p.Lx < 2 || p.Ly < 2 || p.Lx > DQMC_MAX_SIDE || p.Ly > DQMC_MAX_SIDE) return DQMC_ERR_ARG;
+  if ((p.Lx & 1) || (p.Ly & 1)) return DQMC_ERR_ARG;
+  if (!(p.dtau > 0.0) || !(p.beta > 0.0) || !(p.U >= 0.0) || !std::isfinite(p.t)) return DQMC_ERR_ARG;
+  const double r = p.beta / p.dtau;
+  const long long L = std::llround(r);
+  if (L < 1 || std::fabs(r - static_cast<double>(L)) > 1e-9 || L > 100000) return DQMC_ERR_ARG;
+  if (p.n_chains < 1 || p.stab_interval < 1 || p.delay_k < 1 || p.delay_k > DQMC_MAX_DELAY)
+    return DQMC_ERR_ARG;
+  if (p.precision != DQMC_FP64 && p.precision != DQMC_FP32) return DQMC_ERR_ARG;
+  return DQMC_OK;
+}
+
+int setup_group(dqmc_ctx* ctx, Group& g) {
+  const dqmc_group& p = g.p;
+  g.N = p.Lx * p.Ly;
+  g.L = static_cast<int>(std::llround(p.beta / p.dtau));
+  g.C = p.n_chains;
+  g.lam = std::acosh(std::exp(0.5 * p.dtau * p.U));
+  g.cp.clear();
+  for (int j = 0;; ++j) {
+    const int c = std::min(j * p.stab_interval, g.L);
+    g.cp.push_back(c);
+    if (c == g.L) break;
+  }
+  g.nc = static_cast<int>(g.cp.size()) - 1;
+  ring_taps(p.Lx, p.t, p.dtau, g.taps.ex, g.taps.exi);
+  ring_taps(p.Ly, p.t, p.dtau, g.taps.ey, g.taps.eyi);
+  const size_t C = g.C, N = g.N, NN = N * N, S = static_cast<size_t>(g.nc + 1);
+  const size_t tsz = p.precision == DQMC_FP32 ? 4 : 8;
+  DQ_RET(dev_alloc(ctx, &g.field, C * g.L * N));
+  DQ_RET(dev_alloc(ctx, &g.Gw, C * NN * tsz));
+  DQ_RET(dev_alloc(ctx, &g.G64, C * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.RU, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.RT, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.RD, C * S * N * 8));
+  DQ_RET(dev_alloc(ctx, &g.LU, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.LT, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.LD, C * S * N * 8));
+  DQ_RET(dev_alloc(ctx, &g.X, C * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.Rtil, C * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.Mid, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.W1, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.W2, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.A1, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.A2, C * S * NN * 8));
+  DQ_RET(dev_alloc(ctx, &g.logabs, C * S * 8));
+  DQ_RET(dev_alloc(ctx, &g.obs, C * 4 * 8));
+  DQ_RET(dev_alloc(ctx, &g.drift, C * 8));
+  DQ_RET(dev_alloc(ctx, &g.acc, C * 8));
+  DQ_RET(dev_alloc(ctx, &g.bins, C * (g.L + 1) * 2 * N * 8));
+  DQ_RET(dev_alloc(ctx, &g.gacc, C * 3 * 8));
+  DQ_RET(dev_alloc(ctx, &g.gout, C * (g.L + 1) * N * 8));
+  std::vector<int> cpg = g.cp, cpd = g.cp;
+  cpg.push_back(g.L + 1);
+  cpd.push_back(g.L);
+  DQ_RET(dev_alloc(ctx, &g.d_cp_gtau, cpg.size() * sizeof(int)));
+  DQ_RET(dev_alloc(ctx, &g.d_cp_grad, cpd.size() * sizeof(int)));
+  DQ_CK(cudaMemcpyAsync(g.d_cp_gtau, cpg.data(), cpg.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        ctx->st));
+  DQ_CK(cudaMemcpyAsync(g.d_cp_grad, cpd.data(), cpd.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        ctx->st));
+  DQ_CK(cudaMemsetAsync(g.obs, 0, C * 4 * 8, ctx->st));
+  DQ_CK(cudaMemsetAsync(g.drift, 0, C * 8, ctx->st));
+  DQ_CK(cudaMemsetAsync(g.acc, 0, C * 8, ctx->st));
+  return DQMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dqmc_strerror(int code) {
+  switch (code) {
+    case DQMC_OK: return "ok";
+    case DQMC_ERR_ARG: return "invalid argument";
+    case DQMC_ERR_CUDA: return "CUDA error";
+    case DQMC_ERR_OOM: return "device out of memory";
+    case DQMC_ERR_DRIFT: return "Green-function drift above limit";
+    case DQMC_ERR_TIMEOUT: return "device-side wait timed out";
+    case DQMC_ERR_NAN: return "non-finite or singular value in a stabilised matrix";
+    case DQMC_ERR_STATE: return "call not valid in the current state";
+    default: return "unknown error";
+  }
+}
+
+void dqmc_destroy(dqmc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  for (void* p : ctx->allocs) cudaFree(p);
+  delete ctx;
+}
+
+int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* stream, dqmc_ctx** out) {
+  if (!groups || n_groups < 1 || !out) return DQMC_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n_groups; ++i) DQ_RET(validate(groups[i]));
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
+      prop.major * 10 + prop.minor < 100)
+    return DQMC_ERR_CUDA;
+  dqmc_ctx* ctx = new (std::nothrow) dqmc_ctx();
+  if (!ctx) return DQMC_ERR_OOM;
+  ctx->st = static_cast<cudaStream_t>(stream);
+  ctx->seed = seed;
+  ctx->g.resize(n_groups);
+  int rc = dev_alloc(ctx, &ctx->d_sweep, sizeof(uint32_t));
+  if (rc == DQMC_OK) rc = dev_alloc(ctx, &ctx->d_status, sizeof(int));
+  if (rc == DQMC_OK) {
+    if (cudaMemsetAsync(ctx->d_sweep, 0, sizeof(uint32_t), ctx->st) != cudaSuccess ||
+        cudaMemsetAsync(ctx->d_status, 0, sizeof(int), ctx->st) != cudaSuccess)
+      rc = DQMC_ERR_CUDA;
+  }
+  int chain0 = 0;
+  for (int i = 0; i < n_groups && rc == DQMC_OK; ++i) {
+    Group& g = ctx->g[i];
+    g.p = groups[i];
+    g.chain0 = chain0;
+    rc = setup_group(ctx, g);
+    chain0 += g.C;
+    if (rc == DQMC_OK) {
+      ++ctx->launches;
+      if (launch_init_field(g.field, g.C, g.L, g.N, g.chain0, seed, ctx->st) != cudaSuccess)
+        rc = DQMC_ERR_CUDA;
+    }
+    if (rc == DQMC_OK) rc = rebuild(ctx, g);
+    if (rc == DQMC_OK) {
+      ++ctx->launches;
+      if (g.p.precision == DQMC_FP32)
+        rc = launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), ctx->st) ==
+                     cudaSuccess ? DQMC_OK : DQMC_ERR_CUDA;
+      else
+        rc = launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st) ==
+                     cudaSuccess ? DQMC_OK : DQMC_ERR_CUDA;
+    }
+  }
+  ctx->total = chain0;
+  if (rc == DQMC_OK) rc = check_status(ctx);
+  if (rc != DQMC_OK) {
+    dqmc_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return DQMC_OK;
+}
+
+int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure) {
+  if (!ctx || n_sweeps < 0) return DQMC_ERR_ARG;
+  for (int s = 0; s < n_sweeps; ++s) {
+    for (Group& g : ctx->g) DQ_RET(sweep_group(ctx, g, measure));
+    DQ_CLASS(ctx, kTMisc);
+    DQ_LAUNCH(ctx, (k_increment<<<1, 1, 0, ctx->st>>>(ctx->d_sweep), cudaGetLastError()));
+  }
+  return DQMC_OK;
+}
+
+int dqmc_recompute_G(dqmc_ctx* ctx, double* max_drift_out) {
+  if (!ctx) return DQMC_ERR_ARG;
+  std::vector<double> saved;
+  int off = 0;
+  for (Group& g : ctx->g) {
+    DQ_CK(cudaMemsetAsync(g.drift, 0, g.C * sizeof(double), ctx->st));
+    DQ_RET(rebuild(ctx, g));
+    DQ_RET(drift_reset_any(ctx, g));
+    if (max_drift_out)
+      DQ_CK(cudaMemcpyAsync(max_drift_out + off, g.drift, g.C * sizeof(double),
+                            cudaMemcpyDeviceToHost, ctx->st));
+    off += g.C;
+  }
+  return check_status(ctx);
+}
+
+int64_t dqmc_gtau_size(const dqmc_ctx* ctx) {
+  if (!ctx) return DQMC_ERR_ARG;
+  int64_t s = 0;
+  for (const Group& g : ctx->g) s += static_cast<int64_t>(g.C) * (g.L + 1) * g.N;
+  return s;
+}
+
+int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
+  if (!ctx || !out) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (Group& g : ctx->g) {
+    const int batch = g.C * (g.nc + 1);
+    DQ_RET(all_points_w1(ctx, g));
+    // G(c,0)^T = T_R^T Ds_R W1^T  and  W2 = T_L^T Ds_L Mid^{-1}, Y = W2 Db_R^{-1} U_R^T
+    GemmArgs m = gemm0(g.N);
+    m.A = g.RT; m.sA = g.nn(); m.tA = 1;
+    m.ks = g.RD; m.sks = g.N; m.ks_mode = 3;
+    m.B = g.W1; m.sB = g.nn(); m.tB = 1;
+    m.C = g.A1; m.sC = g.nn();
+    DQ_CLASS(ctx, kTGemm);
+    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    m = gemm0(g.N);
+    m.A = g.LT; m.sA = g.nn(); m.tA = 1;
+    m.ks = g.LD; m.sks = g.N; m.ks_mode = 3;
+    m.B = g.Mid; m.sB = g.nn();
+    m.C = g.W2; m.sC = g.nn();
+    DQ_CLASS(ctx, kTGemm);
+    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    m = gemm0(g.N);
+    m.A = g.W2; m.sA = g.nn();
+    m.ks = g.RD; m.sks = g.N; m.ks_mode = 2;
+    m.B = g.RU; m.sB = g.nn();
+    m.C = g.A2; m.sC = g.nn();
+    DQ_CLASS(ctx, kTGemm);
+    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    const long long nb = static_cast<long long>(g.C) * (g.L + 1) * 2 * g.N;
+    DQ_CLASS(ctx, kTMisc);
+    DQ_LAUNCH(ctx, (k_zero<<<static_cast<int>(std::min<long long>((nb + 255) / 256, 1024)), 256, 0,
+                             ctx->st>>>(g.bins, nb),
+                    cudaGetLastError()));
+    GtauArgs ga{};
+    ga.N = g.N; ga.Lx = g.p.Lx; ga.Ly = g.p.Ly; ga.L = g.L;
+    ga.nv = kron_nv(g, true);
+    ga.per_chain = g.nc + 1;
+    ga.c = g.lam;
+    ga.taps = g.taps;
+    ga.field = g.field;
+    ga.cp = g.d_cp_gtau;
+    ga.mat_stride = g.nn();
+    ga.bins = g.bins;
+    ga.kind = kB; ga.vec_is_col = 1; ga.bin_slot = 0;
+    DQ_CLASS(ctx, kTGtauProp);
+    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A1, batch, ga, ctx->st));
+    ga.kind = kBIT; ga.vec_is_col = 0; ga.bin_slot = 1;
+    DQ_CLASS(ctx, kTGtauProp);
+    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, ctx->st));
+    const size_t cnt = static_cast<size_t>(g.C) * (g.L + 1) * g.N;
+    if (out_on_device) {
+      DQ_CLASS(ctx, kTGtauFinal);
+      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, out + off, g.C, g.L, g.p.Lx, g.p.Ly, ctx->st));
+    } else {
+      DQ_CLASS(ctx, kTGtauFinal);
+      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, g.gout, g.C, g.L, g.p.Lx, g.p.Ly, ctx->st));
+      DQ_CK(cudaMemcpyAsync(out + off, g.gout, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    }
+    off += cnt;
+  }
+  if (!out_on_device) return check_status(ctx);
+  return DQMC_OK;
+}
+
+int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda, double* logW,
+              int out_on_device) {
+  if (!ctx) return DQMC_ERR_ARG;
+  int off = 0;
+  for (Group& g : ctx->g) {
+    const int batch = g.C * (g.nc + 1);
+    DQ_RET(all_points_w1(ctx, g));
+    // G at every stabilisation point: W1 Db_R^{-1} U_R^T
+    GemmArgs m = gemm0(g.N);
+    m.A = g.W1; m.sA = g.nn();
+    m.ks = g.RD; m.sks = g.N; m.ks_mode = 2;
+    m.B = g.RU; m.sB = g.nn();
+    m.C = g.A1; m.sC = g.nn();
+    DQ_CLASS(ctx, kTGemm);
+    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    DQ_CK(cudaMemsetAsync(g.gacc, 0, g.C * 3 * sizeof(double), ctx->st));
+    int maxlen = 0;
+    for (int j = 0; j < g.nc; ++j) maxlen = std::max(maxlen, g.cp[j + 1] - g.cp[j]);
+    KronArgs wl = kron_base(g, kB, kron_nv(g, true));
+    KronArgs wr = kron_base(g, kBIT, kron_nv(g, true));
+    wl.per_chain = wr.per_chain = g.nc + 1;
+    wl.cp = wr.cp = g.d_cp_grad;
+    for (int step = 0; step < maxlen; ++step) {
+      DQ_CLASS(ctx, kTGrad);
+      DQ_LAUNCH(ctx, launch_grad_terms(g.A1, g.nn(), g.nc + 1, g.d_cp_grad, step, g.p.Lx, g.p.Ly,
+                                       g.L, g.field, g.p.dtau, g.gacc, batch, ctx->st));
+      if (step + 1 < maxlen) {
+        wl.step = wr.step = step;
+        DQ_CLASS(ctx, kTGrad);
+        DQ_LAUNCH(ctx, launch_kron_cols<double>(g.A1, batch, wl, ctx->st));
+        DQ_CLASS(ctx, kTGrad);
+        DQ_LAUNCH(ctx, launch_kron_rows<double>(g.A1, g.A1, batch, wr, ctx->st));
+      }
+    }
+    // results into W2 scratch: [0, C) dt, [C, 2C) dlambda, [2C, 3C) logW
+    double* tmp = g.W2;
+    DQ_CLASS(ctx, kTMisc);
+    DQ_LAUNCH(ctx, (k_pick3<<<1, 256, 0, ctx->st>>>(g.gacc, tmp, tmp + g.C, g.C), cudaGetLastError()));
+    DQ_CLASS(ctx, kTMisc);
+    DQ_LAUNCH(ctx, (k_logw<<<g.C, 256, 0, ctx->st>>>(g.LD, static_cast<long long>(g.nc + 1) * g.N,
+                                                      g.logabs, g.nc + 1, g.field, g.L, g.N, g.lam,
+                                                      tmp + 2 * g.C),
+                    cudaGetLastError()));
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (dlogW_dt) DQ_CK(cudaMemcpyAsync(dlogW_dt + off, tmp, g.C * 8, kind, ctx->st));
+    if (dlogW_dlambda) DQ_CK(cudaMemcpyAsync(dlogW_dlambda + off, tmp + g.C, g.C * 8, kind, ctx->st));
+    if (logW) DQ_CK(cudaMemcpyAsync(logW + off, tmp + 2 * g.C, g.C * 8, kind, ctx->st));
+    off += g.C;
+  }
+  if (!out_on_device) return check_status(ctx);
+  return DQMC_OK;
+}
+
+int64_t dqmc_field_size(const dqmc_ctx* ctx) {
+  if (!ctx) return DQMC_ERR_ARG;
+  int64_t s = 0;
+  for (const Group& g : ctx->g) s += static_cast<int64_t>(g.C) * g.L * g.N;
+  return s;
+}
+
+int dqmc_get_field(const dqmc_ctx* ctx, int8_t* out) {
+  if (!ctx || !out) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (const Group& g : ctx->g) {
+    const size_t n = static_cast<size_t>(g.C) * g.L * g.N;
+    DQ_CK(cudaMemcpyAsync(out + off, g.field, n, cudaMemcpyDeviceToHost, ctx->st));
+    off += n;
+  }
+  DQ_CK(cudaStreamSynchronize(ctx->st));
+  return DQMC_OK;
+}
+
+int dqmc_set_field(dqmc_ctx* ctx, const int8_t* in) {
+  if (!ctx || !in) return DQMC_ERR_ARG;
+  const int64_t total = dqmc_field_size(ctx);
+  for (int64_t e = 0; e < total; ++e)
+    if (in[e] != 1 && in[e] != -1) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (Group& g : ctx->g) {
+    const size_t n = static_cast<size_t>(g.C) * g.L * g.N;
+    DQ_CK(cudaMemcpyAsync(g.field, in + off, n, cudaMemcpyHostToDevice, ctx->st));
+    off += n;
+    DQ_RET(rebuild(ctx, g));
+    ++ctx->launches;
+    if (g.p.precision == DQMC_FP32)
+      DQ_CK(launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), ctx->st));
+    else
+      DQ_CK(launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st));
+  }
+  return check_status(ctx);
+}
+
+int dqmc_get_G(const dqmc_ctx* ctx, int chain, int spin, double* out) {
+  if (!ctx || !out || chain < 0 || chain >= ctx->total || (spin != 0 && spin != 1))
+    return DQMC_ERR_ARG;
+  for (const Group& g : ctx->g) {
+    if (chain >= g.chain0 + g.C) continue;
+    const int c = chain - g.chain0;
+    DQ_CK(cudaMemcpyAsync(out, g.G64 + c * g.nn(), g.nn() * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->st));
+    DQ_CK(cudaStreamSynchronize(ctx->st));
+    if (spin == 1) {
+      const int N = g.N, Lx = g.p.Lx;
+      std::vector<double> up(out, out + g.nn());
+      for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j) {
+          const int pij = ((i % Lx + i / Lx + j % Lx + j / Lx) & 1) ? -1 : 1;
+          out[static_cast<size_t>(i) * N + j] =
+              (i == j ? 1.0 : 0.0) - pij * up[static_cast<size_t>(j) * N + i];
+        }
+    }
+    return DQMC_OK;
+  }
+  return DQMC_ERR_ARG;
+}
+
+int dqmc_get_observables(const dqmc_ctx* ctx, double* out) {
+  if (!ctx || !out) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (const Group& g : ctx->g) {
+    DQ_CK(cudaMemcpyAsync(out + off, g.obs, g.C * 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                          ctx->st));
+    off += static_cast<size_t>(g.C) * 4;
+  }
+  DQ_CK(cudaStreamSynchronize(ctx->st));
+  return DQMC_OK;
+}
+
+int dqmc_reset_observables(dqmc_ctx* ctx) {
+  if (!ctx) return DQMC_ERR_ARG;
+  for (Group& g : ctx->g) DQ_CK(cudaMemsetAsync(g.obs, 0, g.C * 4 * sizeof(double), ctx->st));
+  return DQMC_OK;
+}
+
+int dqmc_get_stats(const dqmc_ctx* ctx, double* max_drift, uint64_t* accepted) {
+  if (!ctx) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (const Group& g : ctx->g) {
+    if (max_drift)
+      DQ_CK(cudaMemcpyAsync(max_drift + off, g.drift, g.C * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->st));
+    if (accepted)
+      DQ_CK(cudaMemcpyAsync(accepted + off, g.acc, g.C * sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                            ctx->st));
+    off += g.C;
+  }
+  return check_status(const_cast<dqmc_ctx*>(ctx));
+}
+
+int dqmc_reset_stats(dqmc_ctx* ctx) {
+  if (!ctx) return DQMC_ERR_ARG;
+  for (Group& g : ctx->g) {
+    DQ_CK(cudaMemsetAsync(g.drift, 0, g.C * sizeof(double), ctx->st));
+    DQ_CK(cudaMemsetAsync(g.acc, 0, g.C * sizeof(uint64_t), ctx->st));
+  }
+  return DQMC_OK;
+}
+
+int dqmc_num_chains(const dqmc_ctx* ctx) { return ctx ? ctx->total : DQMC_ERR_ARG; }
+
+int64_t dqmc_launch_count(const dqmc_ctx* ctx) { return ctx ? ctx->launches : DQMC_ERR_ARG; }
+
+int dqmc_timing_enable(dqmc_ctx* ctx, int on) {
+  if (!ctx) return DQMC_ERR_ARG;
+  if (on && ctx->ev.empty()) {
+    const size_t pairs = 4096;
+    ctx->ev.resize(2 * pairs);
+    ctx->ev_class.resize(pairs);
+    for (cudaEvent_t& e : ctx->ev) DQ_CK(cudaEventCreate(&e));
+  }
+  if (!on) DQ_RET(timing_fold(ctx));
+  ctx->timing = on != 0;
+  return DQMC_OK;
+}
+
+int dqmc_timing_read(dqmc_ctx* ctx, double* ms, int64_t* launches, int n_classes) {
+  if (!ctx || n_classes < 0) return DQMC_ERR_ARG;
+  DQ_RET(timing_fold(ctx));
+  for (int c = 0; c < n_classes && c < kTNumClasses; ++c) {
+    if (ms) ms[c] = ctx->tms[c];
+    if (launches) launches[c] = ctx->tcount[c];
+  }
+  return kTNumClasses;
+}
+
+int dqmc_timing_reset(dqmc_ctx* ctx) {
+  if (!ctx) return DQMC_ERR_ARG;
+  DQ_RET(timing_fold(ctx));
+  for (int c = 0; c < kTNumClasses; ++c) {
+    ctx->tms[c] = 0.0;
+    ctx->tcount[c] = 0;
+  }
+  return DQMC_OK;
+}
+
+const char* dqmc_timing_class_name(int c) {
+  return (c >= 0 && c < kTNumClasses) ? kTimingNames[c] : "";
+}
+
+}  // extern "C"

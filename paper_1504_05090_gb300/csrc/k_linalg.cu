@@ -1,0 +1,600 @@
+// FP64 linear algebra of libdqmc: the UDV stabilisation of the B-matrix
+// chain and the stabilised Green functions built from it.
+//
+// Paper: Rost & Bluemer, arXiv:1504.05090, Sec. 2 -- the determinants of
+// Eq. (3) and the Green functions G_ij(tau_l) need the products
+// B_l ... B_1 (cost O(Lambda N^3)), which are numerically unstable at low
+// temperature.  They are kept as U diag(D) T (U orthogonal, D graded, T well
+// conditioned) by Householder QR with column pivoting, and G is formed with
+// D split into Db = max(D,1) and Ds = min(D,1):
+//   I + R L = U_R Db_R Mid Db_L U_L^T,
+//   Mid = Db_R^{-1} (U_R^T U_L) Db_L^{-1} + Ds_R (T_R T_L^T) Ds_L,
+// for R = U_R D_R T_R and L^T = U_L D_L T_L.
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dqmc {
+
+__device__ __forceinline__ double scale_of(const double* p, int mode, int i) {
+  if (mode == 0 || p == nullptr) return 1.0;
+  const double d = p[i];
+  switch (mode) {
+    case 1: return d;
+    case 2: return 1.0 / fmax(d, 1.0);
+    case 3: return fmin(d, 1.0);
+    default: return 1.0 / d;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Batched FP64 GEMM, 64x64 output tile per CTA, 16x16 threads with 4x4 each.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gemm_f64(GemmArgs a) {
+  const int b = blockIdx.z;
+  const int n = a.n;
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const double* A = a.A + b * a.sA;
+  const double* B = a.B + b * a.sB;
+  double* C = a.C + b * a.sC;
+  const double* rs = a.rs ? a.rs + b * a.srs : nullptr;
+  const double* ks = a.ks ? a.ks + b * a.sks : nullptr;
+  const double* cs = a.cs ? a.cs + b * a.scs : nullptr;
+  __shared__ double As[16][64 + 2];
+  __shared__ double Bs[16][64 + 2];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    for (int e = threadIdx.x; e < 1024; e += 256) {
+      int ii, kk;
+      double v = 0.0;
+      if (a.tA == 0) {
+        ii = e >> 4;
+        kk = e & 15;
+        if (i0 + ii < n && k0 + kk < n) v = A[static_cast<size_t>(i0 + ii) * n + k0 + kk];
+      } else {
+        kk = e >> 6;
+        ii = e & 63;
+        if (i0 + ii < n && k0 + kk < n) v = A[static_cast<size_t>(k0 + kk) * n + i0 + ii];
+      }
+      if (k0 + kk < n) v *= scale_of(ks, a.ks_mode, k0 + kk);
+      As[kk][ii] = v;
+      int jj;
+      double w = 0.0;
+      if (a.tB == 0) {
+        kk = e >> 6;
+        jj = e & 63;
+        if (k0 + kk < n && j0 + jj < n) w = B[static_cast<size_t>(k0 + kk) * n + j0 + jj];
+      } else {
+        jj = e >> 4;
+        kk = e & 15;
+        if (k0 + kk < n && j0 + jj < n) w = B[static_cast<size_t>(j0 + jj) * n + k0 + kk];
+      }
+      Bs[kk][jj] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty * 4 + r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) bv[q] = Bs[kk][tx * 4 + q];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = fma(av[r], bv[q], acc[r][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty * 4 + r;
+    if (i >= n) continue;
+    const double rsv = a.alpha * scale_of(rs, a.rs_mode, i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int j = j0 + tx * 4 + q;
+      if (j >= n) continue;
+      double v = rsv * acc[r][q] * scale_of(cs, a.cs_mode, j);
+      const size_t o = static_cast<size_t>(i) * n + j;
+      if (a.beta != 0.0) v += a.beta * C[o];
+      C[o] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions.
+// ---------------------------------------------------------------------------
+struct ArgMax {
+  double v;
+  int i;
+};
+
+__device__ __forceinline__ ArgMax argmax_combine(ArgMax a, ArgMax b) {
+  if (b.v > a.v || (b.v == a.v && b.i < a.i)) return b;
+  return a;
+}
+
+__device__ ArgMax block_argmax(ArgMax x, ArgMax* sbuf) {
+  for (int o = 16; o > 0; o >>= 1) {
+    ArgMax y;
+    y.v = __shfl_xor_sync(0xFFFFFFFFu, x.v, o);
+    y.i = __shfl_xor_sync(0xFFFFFFFFu, x.i, o);
+    x = argmax_combine(x, y);
+  }
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sbuf[w] = x;
+  __syncthreads();
+  ArgMax r = sbuf[0];
+  for (int q = 1; q < nw; ++q) r = argmax_combine(r, sbuf[q]);
+  return r;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Householder QR with column pivoting (partial column norms downdated, with
+// recomputation when cancellation is detected, as in LAPACK's xLAQP2), one
+// CTA per matrix.  Storage is X^T row-major so that a column of X is a
+// contiguous row; one warp updates one column at a time.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_qrp(double* Xall, long long sX, double* Qall, long long sQ,
+                                            double* Dall, long long sD, double* Rall, long long sR,
+                                            int n, int* status) {
+  const int b = blockIdx.x;
+  double* X = Xall + b * sX;
+  double* Qt = Qall + b * sQ;
+  double* D = Dall + b * sD;
+  double* Rt = Rall + b * sR;
+  __shared__ double vn1[kMaxN], vn2[kMaxN], vsh[kMaxN], taus[kMaxN];
+  __shared__ int perm[kMaxN];
+  __shared__ ArgMax sred[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double tol3z = sqrt(DBL_EPSILON);
+
+  for (int c = w; c < n; c += nw) {
+    double s = 0.0;
+    for (int r = lane; r < n; r += 32) {
+      const double x = X[static_cast<size_t>(c) * n + r];
+      s += x * x;
+    }
+    s = warp_sum(s);
+    if (lane == 0) {
+      vn1[c] = sqrt(s);
+      vn2[c] = vn1[c];
+      perm[c] = c;
+    }
+  }
+  __syncthreads();
+
+  for (int j = 0; j < n; ++j) {
+    ArgMax m{-1.0, n};
+    for (int c = j + threadIdx.x; c < n; c += blockDim.x) m = argmax_combine(m, ArgMax{vn1[c], c});
+    int p = block_argmax(m, sred).i;
+    if (p < j || p >= n) {  // only non-finite norms left: keep the column, flag it
+      if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
+      p = j;
+    }
+    if (p != j) {
+      for (int r = threadIdx.x; r < n; r += blockDim.x) {
+        const double t = X[static_cast<size_t>(j) * n + r];
+        X[static_cast<size_t>(j) * n + r] = X[static_cast<size_t>(p) * n + r];
+        X[static_cast<size_t>(p) * n + r] = t;
+      }
+      if (threadIdx.x == 0) {
+        int ti = perm[j]; perm[j] = perm[p]; perm[p] = ti;
+        double tv = vn1[j]; vn1[j] = vn1[p]; vn1[p] = tv;
+        tv = vn2[j]; vn2[j] = vn2[p]; vn2[p] = tv;
+      }
+    }
+    __syncthreads();
+    double* xj = X + static_cast<size_t>(j) * n;
+    if (w == 0) {
+      double sig = 0.0;
+      for (int r = j + 1 + lane; r < n; r += 32) sig += xj[r] * xj[r];
+      sig = warp_sum(sig);
+      const double alpha = xj[j];
+      double tau = 0.0, beta = alpha, scal = 1.0;
+      if (sig != 0.0) {
+        const double nr = sqrt(alpha * alpha + sig);
+        beta = (alpha <= 0.0) ? nr : -nr;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      for (int r = j + 1 + lane; r < n; r += 32) xj[r] *= scal;
+      __syncwarp();
+      if (lane == 0) {
+        xj[j] = beta;
+        taus[j] = tau;
+      }
+    }
+    __syncthreads();
+    for (int r = j + threadIdx.x; r < n; r += blockDim.x) vsh[r] = (r == j) ? 1.0 : xj[r];
+    __syncthreads();
+    const double tau = taus[j];
+    for (int c = j + 1 + w; c < n; c += nw) {
+      double* xc = X + static_cast<size_t>(c) * n;
+      double s = 0.0;
+      for (int r = j + lane; r < n; r += 32) s += vsh[r] * xc[r];
+      s = warp_sum(s) * tau;
+      for (int r = j + lane; r < n; r += 32) xc[r] -= s * vsh[r];
+      __syncwarp();
+      if (lane == 0 && vn1[c] != 0.0) {
+        double t = fabs(xc[j]) / vn1[c];
+        t = fmax(0.0, 1.0 - t * t);
+        const double q = vn1[c] / vn2[c];
+        if (t * q * q <= tol3z) vn1[c] = -1.0;  // flag: recompute below
+        else vn1[c] *= sqrt(t);
+      }
+      __syncwarp();
+      if (vn1[c] < 0.0) {
+        double s2 = 0.0;
+        for (int r = j + 1 + lane; r < n; r += 32) s2 += xc[r] * xc[r];
+        s2 = warp_sum(s2);
+        __syncwarp();
+        if (lane == 0) {
+          vn1[c] = sqrt(s2);
+          vn2[c] = vn1[c];
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // D = |diag R|, Rtil[i][perm[c]] = R[i][c] / D[i]  (R[i][c] = X[c][i], c >= i).
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double d = fabs(X[static_cast<size_t>(i) * n + i]);
+    if (!(d > 0.0)) {
+      atomicExch(status, kDevSingular);
+      d = DBL_MIN;
+    }
+    D[i] = d;
+  }
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < static_cast<size_t>(n) * n; e += blockDim.x) {
+    const int i = static_cast<int>(e / n), c = static_cast<int>(e - static_cast<size_t>(i) * n);
+    const double v = (c >= i) ? X[static_cast<size_t>(c) * n + i] / D[i] : 0.0;
+    Rt[static_cast<size_t>(i) * n + perm[c]] = v;
+  }
+  // Q = H_0 H_1 ... H_{n-1}, accumulated backwards into Q^T (row c = column c).
+  for (size_t e = threadIdx.x; e < static_cast<size_t>(n) * n; e += blockDim.x) {
+    const int c = static_cast<int>(e / n), r = static_cast<int>(e - static_cast<size_t>(c) * n);
+    Qt[e] = (c == r) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    const double* xj = X + static_cast<size_t>(j) * n;
+    for (int r = j + threadIdx.x; r < n; r += blockDim.x) vsh[r] = (r == j) ? 1.0 : xj[r];
+    __syncthreads();
+    const double tau = taus[j];
+    if (tau != 0.0) {
+      for (int c = j + w; c < n; c += nw) {
+        double* qc = Qt + static_cast<size_t>(c) * n;
+        double s = 0.0;
+        for (int r = j + lane; r < n; r += 32) s += vsh[r] * qc[r];
+        s = warp_sum(s) * tau;
+        for (int r = j + lane; r < n; r += 32) qc[r] -= s * vsh[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// In-place Gauss-Jordan inverse with row pivoting, one CTA per matrix;
+// also log|det| and sign(det).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512) k_gj_inverse(double* Aall, long long sA, int n,
+                                                   double* logabs, double* sgn, int* status) {
+  const int b = blockIdx.x;
+  double* A = Aall + b * sA;
+  __shared__ double prow[kMaxN], fcol[kMaxN];
+  __shared__ int perm[kMaxN];
+  __shared__ ArgMax sred[32];
+  double la = 0.0, sg = 1.0;
+  for (int k = 0; k < n; ++k) {
+    ArgMax m{-1.0, n};
+    for (int i = k + threadIdx.x; i < n; i += blockDim.x)
+      m = argmax_combine(m, ArgMax{fabs(A[static_cast<size_t>(i) * n + k]), i});
+    int p = block_argmax(m, sred).i;
+    if (p < k || p >= n) {  // non-finite column: no valid pivot, flag it
+      if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
+      p = k;
+    }
+    if (p != k) {
+      for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
+        const double t = A[static_cast<size_t>(k) * n + jj];
+        A[static_cast<size_t>(k) * n + jj] = A[static_cast<size_t>(p) * n + jj];
+        A[static_cast<size_t>(p) * n + jj] = t;
+      }
+      sg = -sg;
+    }
+    if (threadIdx.x == 0) perm[k] = p;
+    __syncthreads();
+    double piv = A[static_cast<size_t>(k) * n + k];
+    if (!(fabs(piv) > 0.0)) {
+      if (threadIdx.x == 0) atomicExch(status, kDevSingular);
+      piv = DBL_MIN;
+    }
+    la += log(fabs(piv));
+    if (piv < 0.0) sg = -sg;
+    const double ipiv = 1.0 / piv;
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {
+      const double v = (jj == k) ? ipiv : A[static_cast<size_t>(k) * n + jj] * ipiv;
+      prow[jj] = v;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      fcol[i] = (i == k) ? 0.0 : A[static_cast<size_t>(i) * n + k];
+    __syncthreads();
+    for (size_t e = threadIdx.x; e < static_cast<size_t>(n) * n; e += blockDim.x) {
+      const int i = static_cast<int>(e / n), jj = static_cast<int>(e - static_cast<size_t>(i) * n);
+      if (i == k) {
+        A[e] = prow[jj];
+      } else {
+        const double f = fcol[i];
+        A[e] = (jj == k) ? -f * prow[k] : A[e] - f * prow[jj];
+      }
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t = A[static_cast<size_t>(i) * n + k];
+        A[static_cast<size_t>(i) * n + k] = A[static_cast<size_t>(i) * n + p];
+        A[static_cast<size_t>(i) * n + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (logabs) logabs[b] = la;
+    if (sgn) sgn[b] = sg;
+  }
+}
+
+__global__ void k_set_identity(double* M, long long sM, double* D, long long sD, int n) {
+  const int b = blockIdx.y;
+  for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+       e < static_cast<size_t>(n) * n; e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(e / n), j = static_cast<int>(e - static_cast<size_t>(i) * n);
+    M[b * sM + e] = (i == j) ? 1.0 : 0.0;
+    if (D && j == 0) D[b * sD + i] = 1.0;
+  }
+}
+
+template <typename T>
+__global__ void k_convert(const double* src, T* dst, long long n) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x)
+    dst[e] = static_cast<T>(src[e]);
+}
+
+// ---------------------------------------------------------------------------
+// Unequal-time G: starting from the matrix of a stabilisation point, apply
+// the slice factors of the block and, after each slice, add every element
+// into the bin of its separation r = r_i - r_j.  Vectors are contiguous rows
+// (G(l,0)^T or Y = (I - G(0)) R_l^{-1}).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N, const T* tx,
+                                 const T* ty, const T* pre, const T* post);
+
+__global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a) {
+  const int b = blockIdx.y;
+  const int chain = b / a.per_chain, blk = b - chain * a.per_chain;
+  const int N = a.N, nv = a.nv, ld = N + 1;
+  const int r0 = blockIdx.x * nv;
+  const int nrows = min(nv, N - r0);
+  const int lo = a.cp[blk], hi = a.cp[blk + 1];
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double* v = reinterpret_cast<double*>(sm_raw);
+  double* tmp = v + nv * ld;
+  double* tx = tmp + nv * ld;
+  double* ty = tx + kMaxSide;
+  double* sc = ty + kMaxSide;
+  double* sbin = sc + N;
+  const bool inv = (a.kind == kBIT);
+  if (threadIdx.x < kMaxSide) {
+    tx[threadIdx.x] = inv ? a.taps.exi[threadIdx.x] : a.taps.ex[threadIdx.x];
+    ty[threadIdx.x] = inv ? a.taps.eyi[threadIdx.x] : a.taps.ey[threadIdx.x];
+  }
+  double* X = Xall + static_cast<size_t>(b) * a.mat_stride;
+  for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    v[vi * ld + i] = X[static_cast<size_t>(r0 + vi) * N + i];
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sbin[i] = 0.0;
+  const Geom g{a.Lx, a.Ly, N};
+  const int8_t* f = a.field + static_cast<size_t>(chain) * a.L * N;
+  const double cexp = inv ? -a.c : a.c;
+  const double up = exp(cexp), dn = exp(-cexp);
+  for (int l = lo; l < hi; ++l) {
+    __syncthreads();
+    if (l > lo) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x)
+        sc[i] = f[static_cast<size_t>(l - 1) * N + i] > 0 ? up : dn;
+      __syncthreads();
+      kron_transform_d<double>(v, tmp, nrows, ld, a.Lx, a.Ly, N, tx, ty, sc, nullptr);
+    }
+    for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
+      const int vi = e / N, el = e - vi * N;
+      const int q = r0 + vi;
+      const int sep = a.vec_is_col ? sep_index(el, q, g) : sep_index(q, el, g);
+      atomicAdd(&sbin[sep], v[vi * ld + el]);
+    }
+    __syncthreads();
+    double* out = a.bins + ((static_cast<size_t>(chain) * (a.L + 1) + l) * 2 + a.bin_slot) * N;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      atomicAdd(&out[i], sbin[i]);
+      sbin[i] = 0.0;
+    }
+  }
+}
+
+template <typename T>
+__device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N, const T* tx,
+                                 const T* ty, const T* pre, const T* post) {
+  const int tot = nv * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    const int x = i % Lx, y = i / Lx;
+    const T* row = v + vi * ld + Lx * y;
+    const T* pr = pre ? pre + Lx * y : nullptr;
+    T acc = T(0);
+    for (int xp = 0; xp < Lx; ++xp) {
+      int dd = x - xp;
+      dd += dd < 0 ? Lx : 0;
+      acc += tx[dd] * (pr ? row[xp] * pr[xp] : row[xp]);
+    }
+    tmp[vi * ld + i] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    const int x = i % Lx, y = i / Lx;
+    const T* col = tmp + vi * ld + x;
+    T acc = T(0);
+    for (int yp = 0; yp < Ly; ++yp) {
+      int dd = y - yp;
+      dd += dd < 0 ? Ly : 0;
+      acc += ty[dd] * col[Lx * yp];
+    }
+    v[vi * ld + i] = post ? acc * post[i] : acc;
+  }
+  __syncthreads();
+}
+
+// out[c][l][k] = 1/(2N) sum_r cos(k.r) (binG[r] + (-1)^{rx+ry} binY[r]); the
+// second term is the spin-down G at k from Y at k + (pi, pi).
+__global__ void __launch_bounds__(256) k_gtau_finalize(const double* bins, double* out, int L,
+                                                      int Lx, int Ly) {
+  const int cl = blockIdx.x;  // chain * (L+1) + l
+  const int N = Lx * Ly;
+  const double* bg = bins + static_cast<size_t>(cl) * 2 * N;
+  const double* by = bg + N;
+  __shared__ double fr[kMaxN], hc[kMaxN], hs[kMaxN];
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    const int rx = r % Lx, ry = r / Lx;
+    fr[r] = bg[r] + (((rx + ry) & 1) ? -by[r] : by[r]);
+  }
+  __syncthreads();
+  // hc/hs[kx + Lx ry] = sum_rx cos/sin(2 pi kx rx / Lx) f(rx, ry)
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int kx = e % Lx, ry = e / Lx;
+    double c = 0.0, s = 0.0;
+    for (int rx = 0; rx < Lx; ++rx) {
+      const double ph = 2.0 * ((kx * rx) % Lx) / Lx;
+      c += cospi(ph) * fr[rx + Lx * ry];
+      s += sinpi(ph) * fr[rx + Lx * ry];
+    }
+    hc[e] = c;
+    hs[e] = s;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
+    const int kx = e % Lx, ky = e / Lx;
+    double acc = 0.0;
+    for (int ry = 0; ry < Ly; ++ry) {
+      const double ph = 2.0 * ((ky * ry) % Ly) / Ly;
+      acc += cospi(ph) * hc[kx + Lx * ry] - sinpi(ph) * hs[kx + Lx * ry];
+    }
+    out[static_cast<size_t>(cl) * N + e] = acc / (2.0 * N);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_grad_terms(const double* Gall, long long sG, int per_chain,
+                                                   const int* cp, int step, int Lx, int Ly, int L,
+                                                   const int8_t* field, double dtau, double* acc) {
+  const int b = blockIdx.x;
+  const int chain = b / per_chain, blk = b - chain * per_chain;
+  const int m = cp[blk] + step;
+  if (m >= cp[blk + 1]) return;
+  const int N = Lx * Ly;
+  const double* G = Gall + b * sG;
+  const int8_t* s = field + (static_cast<size_t>(chain) * L + m) * N;
+  double tt = 0.0, tl = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const int x = j % Lx, y = j / Lx;
+    const int nb[4] = {(x + 1) % Lx + Lx * y, (x + Lx - 1) % Lx + Lx * y, x + Lx * ((y + 1) % Ly),
+                       x + Lx * ((y + Ly - 1) % Ly)};
+    for (int q = 0; q < 4; ++q) tt += G[static_cast<size_t>(j) * N + nb[q]];
+    tl += static_cast<double>(s[j]) * (1.0 - 2.0 * G[static_cast<size_t>(j) * N + j]);
+  }
+  tt = warp_sum(tt);
+  tl = warp_sum(tl);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[chain * 3 + 0], -2.0 * dtau * tt);
+    atomicAdd(&acc[chain * 3 + 1], tl);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_gemm(const GemmArgs& a, int batch, cudaStream_t st) {
+  dim3 grid((a.n + 63) / 64, (a.n + 63) / 64, batch);
+  k_gemm_f64<<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_qrp(double* Xt, long long sX, double* Qt, long long sQ, double* D, long long sD,
+                       double* Rtil, long long sR, int n, int batch, int* status, cudaStream_t st) {
+  k_qrp<<<batch, 512, 0, st>>>(Xt, sX, Qt, sQ, D, sD, Rtil, sR, n, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gj_inverse(double* A, long long sA, int n, int batch, double* logabs,
+                              double* sign, int* status, cudaStream_t st) {
+  k_gj_inverse<<<batch, 512, 0, st>>>(A, sA, n, logabs, sign, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_identity(double* M, long long sM, double* D, long long sD, int n, int batch,
+                                cudaStream_t st) {
+  dim3 grid(std::max(1, std::min((n * n + 255) / 256, 64)), batch);
+  k_set_identity<<<grid, 256, 0, st>>>(M, sM, D, sD, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_convert(const double* src, T* dst, long long n, cudaStream_t st) {
+  const int blocks = static_cast<int>(std::min<long long>((n + 255) / 256, 152 * 8));
+  k_convert<T><<<std::max(blocks, 1), 256, 0, st>>>(src, dst, n);
+  return cudaGetLastError();
+}
+template cudaError_t launch_convert<double>(const double*, double*, long long, cudaStream_t);
+template cudaError_t launch_convert<float>(const double*, float*, long long, cudaStream_t);
+
+cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, cudaStream_t st) {
+  const size_t sm = (2ull * a.nv * (a.N + 1) + 2 * kMaxSide + 2ull * a.N) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_gtau_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.N + a.nv - 1) / a.nv, batch);
+  k_gtau_propagate<<<grid, 256, sm, st>>>(X, a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gtau_finalize(const double* bins, double* out, int C, int L, int Lx, int Ly,
+                                 cudaStream_t st) {
+  k_gtau_finalize<<<C * (L + 1), 256, 0, st>>>(bins, out, L, Lx, Ly);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_terms(const double* G, long long sG, int per_chain, const int* cp, int step,
+                              int Lx, int Ly, int L, const int8_t* field, double dtau, double* acc,
+                              int batch, cudaStream_t st) {
+  k_grad_terms<<<batch, 256, 0, st>>>(G, sG, per_chain, cp, step, Lx, Ly, L, field, dtau, acc);
+  return cudaGetLastError();
+}
+
+}  // namespace dqmc

@@ -1,0 +1,505 @@
+// Sweep kernels of libdqmc: HS-field initialisation, the Metropolis pass of
+// one time slice with delayed rank-k Sherman-Morrison updates, Kronecker
+// multiplication by B_l = exp(-dtau K) exp(V_l) (slice wrap and UDV stack
+// products), drift check and equal-time observables.
+//
+// Paper: Rost & Bluemer, arXiv:1504.05090, Sec. 2, Eqs. (1)-(3).  The
+// Metropolis ratio and the Sherman-Morrison update follow from Eq. (3) for a
+// single flip s -> -s of the Ising field (e^{V'} = e^{V}(I + Delta e_i e_i^T)):
+//   R_sigma = 1 + Delta_sigma (1 - G_ii),  Delta_sigma = e^{-2 sigma lambda s} - 1,
+//   G' = G - (Delta/R) (I - G) e_i e_i^T G.
+// Only spin up is evolved: on the bipartite half-filled lattice
+// G_dn = I - P G_up^T P (P = diag((-1)^{x+y})), so G_dn,ii = 1 - G_up,ii.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace dqmc {
+
+// ---------------------------------------------------------------------------
+// Initial Ising field: s = +1 iff word 0 of Philox(i + N*l, ~0, chain, 1) is odd.
+// ---------------------------------------------------------------------------
+__global__ void k_init_field(int8_t* field, int C, int L, int N, int chain0, uint32_t k0,
+                             uint32_t k1) {
+  const long long total = static_cast<long long>(C) * L * N;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e / (static_cast<long long>(L) * N));
+    const int rem = static_cast<int>(e - static_cast<long long>(c) * L * N);  // l*N + i
+    const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(rem), 0xFFFFFFFFu,
+                                             static_cast<uint32_t>(chain0 + c), kTagInitField),
+                                  k0, k1);
+    field[e] = (r.x & 1u) ? int8_t(1) : int8_t(-1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Metropolis pass over the N sites of one slice, one CTA per chain, one
+// thread per row/column index j.  G (row-major, working precision) stays in
+// global memory (L2-resident); accepted flips are buffered as column vectors
+// U[m] and row vectors V[m] in shared memory, G_cur = G + sum_m U[m] V[m]^T,
+// and folded into G every k accepts (delayed rank-k update).  The diagonal of
+// G_cur is tracked in shared memory so that a rejected proposal costs O(1).
+// The accept/reject decision is taken in FP64 by lane 0 of every warp and
+// broadcast with a shuffle, so all threads agree without a barrier.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int cnt, int N, int NP,
+                                              int j) {
+  if (j >= N) return;
+  T v[kMaxDelay];
+#pragma unroll
+  for (int m = 0; m < kMaxDelay; ++m) v[m] = (m < cnt) ? V[m * NP + j] : T(0);
+  for (int r = 0; r < N; ++r) {
+    T acc = G[static_cast<size_t>(r) * N + j];
+#pragma unroll
+    for (int m = 0; m < kMaxDelay; ++m)
+      if (m < cnt) acc += U[m * NP + r] * v[m];
+    G[static_cast<size_t>(r) * N + j] = acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, MetroArgs a) {
+  const int c = blockIdx.x;
+  const int N = a.N;
+  const int NP = blockDim.x;
+  const int j = threadIdx.x;
+  const int lane = j & 31;
+  const bool act = j < N;
+  T* G = Gall + static_cast<size_t>(c) * N * N;
+  int8_t* s_l = fieldall + (static_cast<size_t>(c) * a.L + a.l0) * N;
+
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  double* uu = reinterpret_cast<double*>(sm_raw);  // [NP] proposal uniforms
+  T* U = reinterpret_cast<T*>(uu + NP);             // [k][NP]
+  T* V = U + a.k * NP;                              // [k][NP]
+  T* d = V + a.k * NP;                              // [NP] diag of G_cur
+  int* ss = reinterpret_cast<int*>(d + NP);         // [NP] field of the slice
+
+  const uint32_t sweep = *a.sweep_ctr;
+  if (act) {
+    d[j] = G[static_cast<size_t>(j) * N + j];
+    ss[j] = s_l[j];
+    const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(j + N * a.l0), sweep,
+                                             static_cast<uint32_t>(a.chain0 + c), kTagProposal),
+                                  a.key0, a.key1);
+    uu[j] = uniform53(r.x, r.y);
+  }
+  __syncthreads();
+
+  T colv = T(0), rowv = T(0);
+  if (act) {
+    colv = G[static_cast<size_t>(j) * N];
+    rowv = G[j];
+  }
+  int cnt = 0;
+  unsigned naccept = 0;
+  for (int i = 0; i < N; ++i) {
+    T ncol = T(0), nrow = T(0);
+    if (act && i + 1 < N) {
+      ncol = G[static_cast<size_t>(j) * N + i + 1];
+      nrow = G[static_cast<size_t>(i + 1) * N + j];
+    }
+    int acc_i = 0;
+    double ru = 1.0, du = 0.0;
+    if (lane == 0) {
+      const double g = static_cast<double>(d[i]);
+      const int s = ss[i];
+      du = s > 0 ? a.em2 : a.ep2;
+      const double dd = s > 0 ? a.ep2 : a.em2;
+      ru = 1.0 + du * (1.0 - g);
+      const double rd = 1.0 + dd * g;
+      acc_i = uu[i] < ru * rd;
+    }
+    acc_i = __shfl_sync(0xFFFFFFFFu, acc_i, 0);
+    if (acc_i) {
+      du = __shfl_sync(0xFFFFFFFFu, du, 0);
+      ru = __shfl_sync(0xFFFFFFFFu, ru, 0);
+      ++naccept;
+      const T coef = static_cast<T>(-du / ru);
+      if (act) {
+        T gc = colv, gr = rowv;
+        for (int m = 0; m < cnt; ++m) {
+          gc += U[m * NP + j] * V[m * NP + i];
+          gr += U[m * NP + i] * V[m * NP + j];
+        }
+        const T uj = coef * ((j == i ? T(1) : T(0)) - gc);
+        U[cnt * NP + j] = uj;
+        V[cnt * NP + j] = gr;
+        // d[i] and ss[i] are read by slower warps for this same site; both are
+        // dead for the rest of the slice, so they are left untouched.
+        if (j != i)
+          d[j] += uj * gr;
+        else
+          s_l[i] = static_cast<int8_t>(-ss[i]);
+      }
+      __syncthreads();
+      ++cnt;
+      if (cnt == a.k) {
+        delayed_flush(G, U, V, cnt, N, NP, j);
+        cnt = 0;
+        __syncthreads();
+        if (act && i + 1 < N) {
+          ncol = G[static_cast<size_t>(j) * N + i + 1];
+          nrow = G[static_cast<size_t>(i + 1) * N + j];
+        }
+      }
+    }
+    colv = ncol;
+    rowv = nrow;
+  }
+  if (cnt > 0) delayed_flush(G, U, V, cnt, N, NP, j);
+  if (j == 0) a.accepted[c] += naccept;
+}
+
+// ---------------------------------------------------------------------------
+// Kronecker transform of nv vectors held in shared memory (row stride ld):
+// v <- Ey (x) Ex applied to (pre o v), then multiplied by post.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N,
+                                               const T* tx, const T* ty, const T* pre,
+                                               const T* post) {
+  const int tot = nv * N;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    const int x = i % Lx, y = i / Lx;
+    const T* row = v + vi * ld + Lx * y;
+    T acc = T(0);
+    if (pre) {
+      const T* pr = pre + Lx * y;
+      for (int xp = 0; xp < Lx; ++xp) {
+        int dd = x - xp;
+        dd += dd < 0 ? Lx : 0;
+        acc += tx[dd] * (row[xp] * pr[xp]);
+      }
+    } else {
+      for (int xp = 0; xp < Lx; ++xp) {
+        int dd = x - xp;
+        dd += dd < 0 ? Lx : 0;
+        acc += tx[dd] * row[xp];
+      }
+    }
+    tmp[vi * ld + i] = acc;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    const int x = i % Lx, y = i / Lx;
+    const T* col = tmp + vi * ld + x;
+    T acc = T(0);
+    for (int yp = 0; yp < Ly; ++yp) {
+      int dd = y - yp;
+      dd += dd < 0 ? Ly : 0;
+      acc += ty[dd] * col[Lx * yp];
+    }
+    v[vi * ld + i] = post ? acc * post[i] : acc;
+  }
+  __syncthreads();
+}
+
+// Shared-memory staging common to both Kronecker kernels.
+template <typename T>
+struct KronStage {
+  T* v;
+  T* tmp;
+  T* tx;   // active taps x
+  T* ty;   // active taps y
+  T* sc;   // diag scale of the current slice
+};
+
+template <typename T>
+__device__ __forceinline__ KronStage<T> kron_stage(unsigned char* raw, int nv, int ld) {
+  KronStage<T> s;
+  s.v = reinterpret_cast<T*>(raw);
+  s.tmp = s.v + nv * ld;
+  s.tx = s.tmp + nv * ld;
+  s.ty = s.tx + kMaxSide;
+  s.sc = s.ty + kMaxSide;
+  return s;
+}
+
+// Resolve the slice range of batch entry b (one chain, or one chain x block).
+__device__ __forceinline__ bool kron_entry_range(const KronArgs& a, int b, int* chain, int* first,
+                                                 int* count) {
+  *chain = b / a.per_chain;
+  if (a.cp) {
+    const int blk = b - *chain * a.per_chain;
+    const int lo = a.cp[blk] + a.step, hi = a.cp[blk + 1];
+    *first = lo;
+    *count = (lo < hi) ? 1 : 0;
+    return lo < hi;
+  }
+  *first = a.l0_first;
+  *count = a.n_slices;
+  return a.n_slices > 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void kron_load_taps(const KronArgs& a, KronStage<T> s) {
+  if (threadIdx.x < kMaxSide) {
+    const int t = threadIdx.x;
+    const bool inv = (a.kind == kBIT);
+    s.tx[t] = static_cast<T>(inv ? a.taps.exi[t] : a.taps.ex[t]);
+    s.ty[t] = static_cast<T>(inv ? a.taps.eyi[t] : a.taps.ey[t]);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void kron_load_scale(const KronArgs& a, KronStage<T> s,
+                                                const int8_t* f_l, int N) {
+  const double cexp = (a.kind == kBIT) ? -a.c : a.c;
+  const T up = static_cast<T>(exp(cexp)), dn = static_cast<T>(exp(-cexp));
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s.sc[i] = f_l[i] > 0 ? up : dn;
+}
+
+// Vectors are contiguous rows of each N x N matrix.  Each CTA owns nv rows of
+// one batch entry and applies `count` successive slice factors to them.
+template <typename T>
+__global__ void __launch_bounds__(256) k_kron_rows(const T* in, T* out, KronArgs a) {
+  const int b = blockIdx.y;
+  int chain, first, count;
+  if (!kron_entry_range(a, b, &chain, &first, &count)) return;
+  const int N = a.N, nv = a.nv, ld = N + 1;
+  const int r0 = blockIdx.x * nv;
+  const int nrows = min(nv, N - r0);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  KronStage<T> s = kron_stage<T>(sm_raw, nv, ld);
+  kron_load_taps(a, s);
+  const T* src = in + static_cast<size_t>(b) * a.mat_stride;
+  T* dst = out + static_cast<size_t>(b) * a.out_stride;
+  for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    T val = src[static_cast<size_t>(r0 + vi) * N + i];
+    if (a.vscale) val *= static_cast<T>(a.vscale[static_cast<size_t>(b) * a.vscale_stride + r0 + vi]);
+    s.v[vi * ld + i] = val;
+  }
+  const int8_t* f = a.field + static_cast<size_t>(chain) * a.L * N;
+  for (int st = 0; st < count; ++st) {
+    const int l0 = first + st * a.dir;
+    __syncthreads();
+    kron_load_scale(a, s, f + static_cast<size_t>(l0) * N, N);
+    __syncthreads();
+    if (a.kind == kBT)
+      kron_transform(s.v, s.tmp, nrows, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)nullptr,
+                     (const T*)s.sc);
+    else
+      kron_transform(s.v, s.tmp, nrows, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)s.sc,
+                     (const T*)nullptr);
+  }
+  for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
+    const int vi = e / N, i = e - vi * N;
+    dst[static_cast<size_t>(r0 + vi) * N + i] = s.v[vi * ld + i];
+  }
+}
+
+// Vectors are the columns of each row-major N x N matrix (in place).
+template <typename T>
+__global__ void __launch_bounds__(256) k_kron_cols(T* X, KronArgs a) {
+  const int b = blockIdx.y;
+  int chain, first, count;
+  if (!kron_entry_range(a, b, &chain, &first, &count)) return;
+  const int N = a.N, nv = a.nv, ld = N + 1;
+  const int c0 = blockIdx.x * nv;
+  const int ncols = min(nv, N - c0);
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  KronStage<T> s = kron_stage<T>(sm_raw, nv, ld);
+  kron_load_taps(a, s);
+  T* M = X + static_cast<size_t>(b) * a.mat_stride;
+  for (int e = threadIdx.x; e < ncols * N; e += blockDim.x) {
+    const int i = e / ncols, jj = e - i * ncols;
+    s.v[jj * ld + i] = M[static_cast<size_t>(i) * N + c0 + jj];
+  }
+  const int8_t* f = a.field + static_cast<size_t>(chain) * a.L * N;
+  for (int st = 0; st < count; ++st) {
+    const int l0 = first + st * a.dir;
+    __syncthreads();
+    kron_load_scale(a, s, f + static_cast<size_t>(l0) * N, N);
+    __syncthreads();
+    if (a.kind == kBT)
+      kron_transform(s.v, s.tmp, ncols, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)nullptr,
+                     (const T*)s.sc);
+    else
+      kron_transform(s.v, s.tmp, ncols, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)s.sc,
+                     (const T*)nullptr);
+  }
+  for (int e = threadIdx.x; e < ncols * N; e += blockDim.x) {
+    const int i = e / ncols, jj = e - i * ncols;
+    M[static_cast<size_t>(i) * N + c0 + jj] = s.v[jj * ld + i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Drift check: drift[c] = max(drift[c], max|Gw - G64| / max|G64|), then the
+// working G is replaced by the stabilised one.  One CTA per chain.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) k_drift_reset(const double* G64, T* Gw, int N, double* drift,
+                                                    int* status) {
+  const int c = blockIdx.x;
+  const size_t nn = static_cast<size_t>(N) * N;
+  const double* g = G64 + c * nn;
+  T* w = Gw + c * nn;
+  double md = 0.0, mg = 0.0;
+  bool bad = false;
+  for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
+    const double ge = g[e];
+    bad |= !isfinite(ge);
+    md = fmax(md, fabs(static_cast<double>(w[e]) - ge));
+    mg = fmax(mg, fabs(ge));
+    w[e] = static_cast<T>(ge);
+  }
+  __shared__ double s1[32], s2[32];
+  __shared__ int sb;
+  if (threadIdx.x == 0) sb = 0;
+  for (int o = 16; o > 0; o >>= 1) {
+    md = fmax(md, __shfl_xor_sync(0xFFFFFFFFu, md, o));
+    mg = fmax(mg, __shfl_xor_sync(0xFFFFFFFFu, mg, o));
+  }
+  __syncthreads();
+  if (bad) atomicOr(&sb, 1);
+  if ((threadIdx.x & 31) == 0) {
+    s1[threadIdx.x >> 5] = md;
+    s2[threadIdx.x >> 5] = mg;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w2 = 1; w2 < static_cast<int>(blockDim.x >> 5); ++w2) {
+      md = fmax(md, s1[w2]);
+      mg = fmax(mg, s2[w2]);
+    }
+    const double dr = mg > 0.0 ? md / mg : md;
+    if (!(dr <= drift[c])) drift[c] = dr;  // also propagates NaN
+    if (sb) atomicExch(status, kDevNonFinite);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Equal-time observables of one configuration from the stabilised G_up
+// (G_dn = I - P G_up^T P):  n = (1/N) sum_i [(1 - G_ii) + G_ii],
+// docc = (1/N) sum_i (1 - G_ii) G_ii,
+// ekin = (1/N) sum_sigma sum_ij K_ij <c^dag_i c_j> = (2t/N) sum_j sum_delta G_{j, j+delta}.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_observables(const double* G64, int Lx, int Ly, double t,
+                                                    double* obs) {
+  const int c = blockIdx.x;
+  const int N = Lx * Ly;
+  const double* G = G64 + static_cast<size_t>(c) * N * N;
+  double n = 0.0, dc = 0.0, ek = 0.0;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double g = G[static_cast<size_t>(j) * N + j];
+    n += (1.0 - g) + g;
+    dc += (1.0 - g) * g;
+    const int x = j % Lx, y = j / Lx;
+    const int nb[4] = {(x + 1) % Lx + Lx * y, (x + Lx - 1) % Lx + Lx * y, x + Lx * ((y + 1) % Ly),
+                       x + Lx * ((y + Ly - 1) % Ly)};
+    for (int q = 0; q < 4; ++q) ek += G[static_cast<size_t>(j) * N + nb[q]];
+  }
+  __shared__ double sm[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+    dc += __shfl_xor_sync(0xFFFFFFFFu, dc, o);
+    ek += __shfl_xor_sync(0xFFFFFFFFu, ek, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sm[0][threadIdx.x >> 5] = n;
+    sm[1][threadIdx.x >> 5] = dc;
+    sm[2][threadIdx.x >> 5] = ek;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) {
+      n += sm[0][w];
+      dc += sm[1][w];
+      ek += sm[2][w];
+    }
+    double* o = obs + static_cast<size_t>(c) * 4;
+    o[0] += n / N;
+    o[1] += dc / N;
+    o[2] += 2.0 * t * ek / N;
+    o[3] += 1.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launch wrappers.
+// ---------------------------------------------------------------------------
+cudaError_t launch_init_field(int8_t* field, int C, int L, int N, int chain0, uint64_t seed,
+                              cudaStream_t st) {
+  const long long total = static_cast<long long>(C) * L * N;
+  const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 152 * 16));
+  k_init_field<<<blocks, 256, 0, st>>>(field, C, L, N, chain0, static_cast<uint32_t>(seed),
+                                       static_cast<uint32_t>(seed >> 32));
+  return cudaGetLastError();
+}
+
+template <typename T>
+size_t metropolis_smem(int N, int k) {
+  const int NP = ((N + 31) / 32) * 32;
+  return static_cast<size_t>(NP) * sizeof(double) + 2ull * k * NP * sizeof(T) +
+         static_cast<size_t>(NP) * sizeof(T) + static_cast<size_t>(NP) * sizeof(int);
+}
+
+template <typename T>
+cudaError_t launch_metropolis(T* G, int8_t* field, int C, const MetroArgs& a, cudaStream_t st) {
+  const int NP = ((a.N + 31) / 32) * 32;
+  const size_t sm = metropolis_smem<T>(a.N, a.k);
+  cudaError_t e = cudaFuncSetAttribute(k_metropolis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  k_metropolis<T><<<C, NP, sm, st>>>(G, field, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+size_t kron_smem(int N, int nv) {
+  return (2ull * nv * (N + 1) + 2 * kMaxSide + N) * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_kron_rows(const T* in, T* out, int batch, const KronArgs& a, cudaStream_t st) {
+  const size_t sm = kron_smem<T>(a.N, a.nv);
+  cudaError_t e = cudaFuncSetAttribute(k_kron_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.N + a.nv - 1) / a.nv, batch);
+  k_kron_rows<T><<<grid, 256, sm, st>>>(in, out, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_kron_cols(T* X, int batch, const KronArgs& a, cudaStream_t st) {
+  const size_t sm = kron_smem<T>(a.N, a.nv);
+  cudaError_t e = cudaFuncSetAttribute(k_kron_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(sm));
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.N + a.nv - 1) / a.nv, batch);
+  k_kron_cols<T><<<grid, 256, sm, st>>>(X, a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* drift, int* status,
+                               cudaStream_t st) {
+  k_drift_reset<T><<<C, 256, 0, st>>>(G64, Gw, N, drift, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
+                               cudaStream_t st) {
+  k_observables<<<C, 256, 0, st>>>(G64, Lx, Ly, t, obs);
+  return cudaGetLastError();
+}
+
+#define DQMC_INST(T)                                                                              \
+  template cudaError_t launch_metropolis<T>(T*, int8_t*, int, const MetroArgs&, cudaStream_t);   \
+  template cudaError_t launch_kron_rows<T>(const T*, T*, int, const KronArgs&, cudaStream_t);    \
+  template cudaError_t launch_kron_cols<T>(T*, int, const KronArgs&, cudaStream_t);              \
+  template cudaError_t launch_drift_reset<T>(const double*, T*, int, int, double*, int*,         \
+                                             cudaStream_t);                                      \
+  template size_t metropolis_smem<T>(int, int);
+DQMC_INST(double)
+DQMC_INST(float)
+#undef DQMC_INST
+
+}  // namespace dqmc

@@ -1,0 +1,110 @@
+// Host-side declarations of the libdqmc kernel launchers and their argument
+// blocks (passed to the kernels by value).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace dqmc {
+
+struct MetroArgs {
+  int N, L, l0, k, chain0;
+  uint32_t key0, key1;
+  const uint32_t* sweep_ctr;  // device word: index of the running sweep
+  double em2, ep2;            // exp(-2 lambda) - 1, exp(+2 lambda) - 1
+  unsigned long long* accepted;
+};
+
+struct KronArgs {
+  int N, Lx, Ly, L;
+  int nv;                // vectors per CTA
+  int kind;              // KronKind
+  double c;              // sigma * lambda
+  KronTaps taps;
+  const int8_t* field;   // [chain][L][N]
+  long long mat_stride;  // elements between batch matrices (input / in place)
+  long long out_stride;  // elements between output matrices (k_kron_rows)
+  const double* vscale;  // optional per-vector scale (applied on load)
+  long long vscale_stride;
+  int per_chain;         // batch entries per chain
+  // Fixed slice range (cp == nullptr): factors l0_first, l0_first+dir, ... (n_slices of them).
+  int l0_first, dir, n_slices;
+  // Block mode (cp != nullptr): entry blk of a chain applies factor cp[blk] + step
+  // if it is < cp[blk+1] (0-based slice index), else leaves the matrix as is.
+  const int* cp;
+  int step;
+};
+
+// Batched square FP64 GEMM with diagonal scalings:
+//   C = alpha * diag(rs) op(A) diag(ks) op(B) diag(cs) + beta * C.
+// Scale modes: 0 none, 1 d, 2 1/max(d,1), 3 min(d,1), 4 1/d.
+struct GemmArgs {
+  int n;
+  const double* A; long long sA; int tA;
+  const double* B; long long sB; int tB;
+  double* C; long long sC;
+  const double* rs; long long srs; int rs_mode;
+  const double* ks; long long sks; int ks_mode;
+  const double* cs; long long scs; int cs_mode;
+  double alpha, beta;
+};
+
+cudaError_t launch_init_field(int8_t* field, int C, int L, int N, int chain0, uint64_t seed,
+                              cudaStream_t st);
+template <typename T>
+size_t metropolis_smem(int N, int k);
+template <typename T>
+cudaError_t launch_metropolis(T* G, int8_t* field, int C, const MetroArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_kron_rows(const T* in, T* out, int batch, const KronArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_kron_cols(T* X, int batch, const KronArgs& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* drift, int* status,
+                               cudaStream_t st);
+cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
+                               cudaStream_t st);
+
+cudaError_t launch_gemm(const GemmArgs& a, int batch, cudaStream_t st);
+// Householder QR with column pivoting of X^T stored row-major (row c = column
+// c of X).  Outputs Q^T (row c = column c of Q), D = |diag R| and
+// Rtil = D^{-1} R P^T with X = Q diag(D) Rtil.  X is overwritten.
+cudaError_t launch_qrp(double* Xt, long long sX, double* Qt, long long sQ, double* D, long long sD,
+                       double* Rtil, long long sR, int n, int batch, int* status, cudaStream_t st);
+// In-place Gauss-Jordan inverse with row pivoting; logabs/sign of det (may be null).
+cudaError_t launch_gj_inverse(double* A, long long sA, int n, int batch, double* logabs,
+                              double* sign, int* status, cudaStream_t st);
+cudaError_t launch_set_identity(double* M, long long sM, double* D, long long sD, int n, int batch,
+                                cudaStream_t st);
+template <typename T>
+cudaError_t launch_convert(const double* src, T* dst, long long n, cudaStream_t st);
+
+// Unequal-time propagation with separation bins (see k_linalg.cu).
+struct GtauArgs {
+  int N, Lx, Ly, L, nv, per_chain;
+  int kind;              // kB for G(l,0)^T rows, kBIT for Y rows
+  int vec_is_col;        // 1: vector q is column q of G(l,0); 0: vector q is row q of Y
+  double c;
+  KronTaps taps;
+  const int8_t* field;
+  const int* cp;         // checkpoint slices, per_chain + 1 entries... (block b: cp[b]..cp[b+1])
+  long long mat_stride;
+  double* bins;          // [chain][L+1][2][N]
+  int bin_slot;          // 0 for G(l,0), 1 for Y
+};
+cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, cudaStream_t st);
+// out[chain][l][k] from the bins (spin average, momentum transform).
+cudaError_t launch_gtau_finalize(const double* bins, double* out, int C, int L, int Lx, int Ly,
+                                 cudaStream_t st);
+// Gradient terms of the current equal-time G of every (chain, block) entry
+// whose factor cp[blk] + step exists: acc[chain][0] += -2 dtau sum_j sum_delta G_{j,j+delta}
+// (t derivative, both spins), acc[chain][1] += sum_i s_{l0,i} (1 - 2 G_ii) (lambda).
+cudaError_t launch_grad_terms(const double* G, long long sG, int per_chain, const int* cp, int step,
+                              int Lx, int Ly, int L, const int8_t* field, double dtau, double* acc,
+                              int batch, cudaStream_t st);
+
+}  // namespace dqmc

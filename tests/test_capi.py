@@ -1,0 +1,67 @@
+"""The C-ABI library builds, loads and exports every symbol that
+include/dqmc.h declares (CPU-only: no compute calls)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dqmc.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dqmc_[a-zA-Z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1504_05090_gb300 import build
+    if not os.path.exists(build.LIB):
+        build.build()
+    return build.LIB
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dqmc_init", "dqmc_sweep", "dqmc_recompute_G", "dqmc_measure_Gtau",
+                     "dqmc_grad", "dqmc_destroy", "dqmc_strerror"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_1504_05090_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_strerror_and_argument_checks_without_gpu(libpath):
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    assert lib.dqmc_strerror(0) == b"ok"
+    assert lib.dqmc_strerror(-1) == b"invalid argument"
+    h = ctypes.c_void_p()
+    # rejected before any CUDA call: no groups / odd side / k out of range
+    assert lib.dqmc_init(None, 0, 0, None, ctypes.byref(h)) == -1
+    g = _lib.DqmcGroup(5, 4, 0.25, 2.0, 2.0, 0.125, 1, 4, 4, 0)
+    assert lib.dqmc_init(ctypes.byref(g), 1, 0, None, ctypes.byref(h)) == -1
+    g = _lib.DqmcGroup(4, 4, 0.25, 2.0, 2.0, 0.125, 1, 4, 33, 0)
+    assert lib.dqmc_init(ctypes.byref(g), 1, 0, None, ctypes.byref(h)) == -1
+    g = _lib.DqmcGroup(4, 4, 0.25, 2.0, 2.0, 0.3, 1, 4, 4, 0)  # beta/dtau not an integer
+    assert lib.dqmc_init(ctypes.byref(g), 1, 0, None, ctypes.byref(h)) == -1
+    assert lib.dqmc_sweep(None, 1, 0) == -1
+    assert lib.dqmc_num_chains(None) == -1
+    lib.dqmc_destroy(None)
+
+
+def test_package_fails_loudly_without_library(tmp_path):
+    from paper_1504_05090_gb300 import _lib
+    with pytest.raises(ImportError):
+        _lib.load(str(tmp_path / "missing.so"))

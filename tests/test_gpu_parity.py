@@ -1,0 +1,219 @@
+"""CUDA path against the oracle, element by element, on the same seeds and fields.
+
+Tolerances (FP64 working precision): the Ising field and the accept counts are
+bit-exact; stabilised Green functions agree to 1e-10 relative (max norm);
+observables, G(tau) and the derivatives of log W to 1e-9 relative.  The FP32
+working-precision path is checked on field replay (its stabilisation is FP64)
+and by its drift.
+"""
+import numpy as np
+import pytest
+
+from oracle import dqmc as o
+
+pytestmark = pytest.mark.gpu
+
+GTOL = 1e-10
+
+
+def _sim(groups, seed):
+    import paper_1504_05090_gb300 as pkg
+    return pkg.DQMC(groups, seed=seed)
+
+
+def _grp(Lx, Ly, U=2.0, beta=2.0, dtau=0.125, C=1, ns=4, k=8, prec="fp64", t=0.25):
+    import paper_1504_05090_gb300 as pkg
+    return pkg.Group(Lx=Lx, Ly=Ly, t=t, U=U, beta=beta, dtau=dtau, n_chains=C,
+                     stab_interval=ns, delay_k=k, precision=prec)
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def _params(g):
+    return o.Params(g.Lx, g.Ly, g.t, g.U, g.beta, g.dtau, n_s=g.stab_interval)
+
+
+# -- initial state ----------------------------------------------------------
+def test_initial_fields_match_oracle_across_groups():
+    groups = [_grp(4, 4, C=2), _grp(6, 4, beta=1.0, C=3), _grp(2, 2, beta=0.5, C=1)]
+    with _sim(groups, seed=0x1234_5678_9ABC) as sim:
+        fields = sim.field()
+        chain = 0
+        for g, f in zip(groups, fields):
+            for c in range(g.n_chains):
+                ref = o.initial_field(0x1234_5678_9ABC, chain, g.N, g.L)
+                assert np.array_equal(f[c], ref)
+                chain += 1
+
+
+@pytest.mark.parametrize("Lx,Ly,ns,beta", [(4, 4, 4, 2.0), (6, 6, 5, 2.0), (8, 4, 7, 4.0),
+                                           (2, 2, 3, 1.0)])
+def test_initial_green_matches_oracle(Lx, Ly, ns, beta):
+    g = _grp(Lx, Ly, ns=ns, beta=beta, C=2)
+    with _sim([g], seed=3) as sim:
+        for c in range(2):
+            ch = o.Chain(_params(g), seed=3, chain=c)
+            for spin, sg in ((0, 1), (1, -1)):
+                assert _rel(sim.G(c, spin), ch.green(0, sg)) < GTOL
+
+
+# -- sweeps -----------------------------------------------------------------
+@pytest.mark.parametrize("Lx,Ly,beta,dtau,ns,k,C", [
+    (4, 4, 2.0, 0.125, 4, 4, 2),     # k divides nothing in particular; several flushes per slice
+    (6, 6, 2.0, 0.1, 6, 8, 2),       # N = 36: ragged warp tail; n_s does not divide L = 20
+    (8, 8, 1.0, 0.125, 3, 16, 1),    # N = 64, two k = 16 flushes per slice
+    (2, 2, 1.0, 0.25, 2, 1, 3),      # smallest cluster, rank-1 updates (k = 1)
+])
+def test_sweeps_match_oracle(Lx, Ly, beta, dtau, ns, k, C):
+    g = _grp(Lx, Ly, beta=beta, dtau=dtau, ns=ns, k=k, C=C)
+    p = _params(g)
+    with _sim([g], seed=11) as sim:
+        chains = [o.Chain(p, seed=11, chain=c) for c in range(C)]
+        ref_obs = np.zeros((C, 4))
+        ref_acc = np.zeros(C)
+        for sweep in range(2):
+            sim.sweep(1, measure=True)
+            for c, ch in enumerate(chains):
+                out = ch.sweep()
+                ref_acc[c] += out["accepted"]
+                ref_obs[c, :3] += np.sum(out["obs"], axis=0)
+                ref_obs[c, 3] += len(out["obs"])
+                assert np.array_equal(sim.field()[0][c], ch.field), (sweep, c)
+                assert _rel(sim.G(c, 0), out["G_up"]) < GTOL
+                assert _rel(sim.G(c, 1), out["G_dn"]) < GTOL
+        drift, acc = sim.stats()
+        assert np.array_equal(acc.astype(float), ref_acc)
+        assert np.all(drift < 1e-9)
+        obs = sim.observables()
+        np.testing.assert_array_equal(obs[:, 3], ref_obs[:, 3])
+        np.testing.assert_allclose(obs[:, :3], ref_obs[:, :3], rtol=1e-9, atol=1e-12)
+
+
+def test_two_groups_in_one_context_match_oracle():
+    groups = [_grp(4, 4, beta=1.0, ns=3, k=4, C=2), _grp(6, 4, U=1.0, beta=1.5, dtau=0.25, ns=2, k=8, C=1)]
+    with _sim(groups, seed=5) as sim:
+        sim.sweep(1)
+        chain = 0
+        for gi, g in enumerate(groups):
+            for c in range(g.n_chains):
+                ch = o.Chain(_params(g), seed=5, chain=chain)
+                out = ch.sweep()
+                assert np.array_equal(sim.field()[gi][c], ch.field)
+                assert _rel(sim.G(chain, 0), out["G_up"]) < GTOL
+                chain += 1
+
+
+# -- replayed fields, stabilisation at low temperature -----------------------
+def test_set_field_low_temperature_green():
+    g = _grp(8, 8, U=2.0, beta=20.0, dtau=0.2, ns=8, C=2)
+    p = _params(g)
+    rng = np.random.default_rng(0)
+    fields = rng.choice(np.array([-1, 1], dtype=np.int8), size=(2, g.L, g.N))
+    with _sim([g], seed=0) as sim:
+        sim.set_field([fields])
+        for c in range(2):
+            ch = o.Chain(p, field=fields[c])
+            assert _rel(sim.G(c, 0), ch.green(0, 1)) < GTOL
+        drift = sim.recompute_G()
+        assert np.all(drift < 1e-12)
+
+
+# -- unequal-time G -----------------------------------------------------------
+@pytest.mark.parametrize("Lx,Ly,beta,dtau,ns", [(4, 4, 2.0, 0.125, 4), (6, 4, 2.0, 0.2, 3),
+                                                 (8, 8, 4.0, 0.25, 5)])
+def test_gtau_matches_oracle(Lx, Ly, beta, dtau, ns):
+    g = _grp(Lx, Ly, beta=beta, dtau=dtau, ns=ns, C=2)
+    with _sim([g], seed=21) as sim:
+        sim.sweep(1)
+        gt = sim.gtau()[0]
+        f = sim.field()[0]
+        for c in range(2):
+            ch = o.Chain(_params(g), field=f[c])
+            ref = ch.gtau()
+            np.testing.assert_allclose(gt[c], ref, atol=1e-10 * np.max(np.abs(ref)))
+
+
+def test_gtau_on_device_equals_host():
+    import torch
+    g = _grp(4, 4, C=3)
+    with _sim([g], seed=2) as sim:
+        host = sim.gtau()[0]
+        dev = torch.empty(host.size, dtype=torch.float64, device="cuda")
+        sim.gtau(out=dev)
+        # the separation bins are summed with atomics: equal up to summation order
+        np.testing.assert_allclose(dev.cpu().numpy().reshape(host.shape), host, rtol=0, atol=1e-14)
+
+
+# -- derivatives of log W -------------------------------------------------------
+@pytest.mark.parametrize("Lx,Ly,beta,dtau,ns", [(4, 2, 2.0, 0.125, 4), (4, 4, 2.0, 0.25, 3),
+                                                 (6, 6, 1.0, 0.1, 4)])
+def test_grad_matches_oracle(Lx, Ly, beta, dtau, ns):
+    g = _grp(Lx, Ly, beta=beta, dtau=dtau, ns=ns, C=2)
+    with _sim([g], seed=13) as sim:
+        sim.sweep(1)
+        dt, dl, lw = sim.grad()
+        f = sim.field()[0]
+        for c in range(2):
+            ch = o.Chain(_params(g), field=f[c])
+            rdt, rdl = ch.grad()
+            assert dt[c] == pytest.approx(rdt, rel=1e-9, abs=1e-9)
+            assert dl[c] == pytest.approx(rdl, rel=1e-9, abs=1e-9)
+            assert lw[c] == pytest.approx(ch.logw(), rel=1e-10, abs=1e-9)
+
+
+def test_autograd_function_backward():
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    g = _grp(4, 4, C=3)
+    with _sim([g], seed=4) as sim:
+        t = torch.tensor(0.25, dtype=torch.float64, requires_grad=True)
+        lam = torch.tensor(o.hs_lambda(2.0, 0.125), dtype=torch.float64, requires_grad=True)
+        lw = pkg.LogWeight.apply(sim, t, lam)
+        w = torch.arange(1, 4, dtype=torch.float64, device=lw.device)
+        (lw * w).sum().backward()
+        dt, dl, lw2 = sim.grad()
+        np.testing.assert_allclose(lw.detach().cpu().numpy(), lw2, rtol=1e-12)
+        assert t.grad.item() == pytest.approx(float(np.sum(dt * [1, 2, 3])), rel=1e-12)
+        assert lam.grad.item() == pytest.approx(float(np.sum(dl * [1, 2, 3])), rel=1e-12)
+
+
+# -- FP32 working precision ---------------------------------------------------
+def test_fp32_path_replay_and_drift():
+    g32 = _grp(8, 8, beta=4.0, dtau=0.125, ns=8, k=16, C=2, prec="fp32")
+    g64 = _grp(8, 8, beta=4.0, dtau=0.125, ns=8, k=16, C=2, prec="fp64")
+    with _sim([g32], seed=9) as s32, _sim([g64], seed=9) as s64:
+        f = s64.field()
+        assert np.array_equal(s32.field()[0], f[0])
+        for c in range(2):  # stabilisation is FP64 in both modes
+            assert _rel(s32.G(c, 0), s64.G(c, 0)) < GTOL
+        s32.sweep(2)
+        s64.sweep(2)
+        d32, a32 = s32.stats()
+        d64, a64 = s64.stats()
+        assert np.all(d32 < 1e-4), d32
+        assert np.all(d64 < 1e-9), d64
+        # same accepted fraction to within a few percent (decisions may differ
+        # where |u - R| is below the FP32 rounding of G_ii)
+        assert np.all(np.abs(a32.astype(float) - a64.astype(float)) <= 0.05 * a64 + 5)
+
+
+# -- full-size sample: 16x16, L = 160, 64 chains (the benchmarked launch) -----
+@pytest.mark.slow
+def test_full_size_16x16_sampled_chains():
+    g = _grp(16, 16, U=2.0, beta=20.0, dtau=0.125, ns=10, k=32, C=64)
+    p = _params(g)
+    with _sim([g], seed=0) as sim:
+        f0 = sim.field()[0]
+        for c in (0, 63):
+            assert np.array_equal(f0[c], o.initial_field(0, c, g.N, g.L))
+        ch0 = o.Chain(p, seed=0, chain=0)
+        assert _rel(sim.G(0, 0), ch0.green(0, 1)) < GTOL
+        sim.sweep(1)
+        out = ch0.sweep()
+        assert np.array_equal(sim.field()[0][0], ch0.field)
+        assert _rel(sim.G(0, 0), out["G_up"]) < GTOL
+        drift, acc = sim.stats()
+        assert acc[0] == out["accepted"]
+        assert np.all(drift < 1e-8)
