@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -33,6 +34,13 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 __device__ __forceinline__ double uniform53(uint32_t x0, uint32_t x1) {
   const uint64_t b = ((static_cast<uint64_t>(x0) << 32) | x1) >> 11;
   return static_cast<double>(b) * 0x1.0p-53;
+}
+
+// |x| by clearing the sign bit (exact for every double, NaN stays NaN).  Used
+// instead of the fabs overload set, which under this build's host-constexpr
+// relaxation returned its argument unchanged in device code.
+__device__ __forceinline__ double absd(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFLL);
 }
 
 // Counter tags of the two random streams.

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(512) k_qrp(double* Xall, long long sX, double*
       for (int r = j + lane; r < n; r += 32) xc[r] -= s * vsh[r];
       __syncwarp();
       if (lane == 0 && vn1[c] != 0.0) {
-        double t = fabs(xc[j]) / vn1[c];
+        double t = absd(xc[j]) / vn1[c];
         t = fmax(0.0, 1.0 - t * t);
         const double q = vn1[c] / vn2[c];
         if (t * q * q <= tol3z) vn1[c] = -1.0;  // flag: recompute below
@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(512) k_qrp(double* Xall, long long sX, double*
 
   // D = |diag R|, Rtil[i][perm[c]] = R[i][c] / D[i]  (R[i][c] = X[c][i], c >= i).
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double d = fabs(X[static_cast<size_t>(i) * n + i]);
+    double d = absd(X[static_cast<size_t>(i) * n + i]);
     if (!(d > 0.0)) {
       atomicExch(status, kDevSingular);
       d = DBL_MIN;
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(512) k_gj_inverse(double* Aall, long long sA, 
   for (int k = 0; k < n; ++k) {
     ArgMax m{-1.0, n};
     for (int i = k + threadIdx.x; i < n; i += blockDim.x)
-      m = argmax_combine(m, ArgMax{fabs(A[static_cast<size_t>(i) * n + k]), i});
+      m = argmax_combine(m, ArgMax{absd(A[static_cast<size_t>(i) * n + k]), i});
     int p = block_argmax(m, sred).i;
     if (p < k || p >= n) {  // non-finite column: no valid pivot, flag it
       if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
@@ -319,11 +319,11 @@ __global__ void __launch_bounds__(512) k_gj_inverse(double* Aall, long long sA, 
     if (threadIdx.x == 0) perm[k] = p;
     __syncthreads();
     double piv = A[static_cast<size_t>(k) * n + k];
-    if (!(fabs(piv) > 0.0)) {
+    if (!(absd(piv) > 0.0)) {
       if (threadIdx.x == 0) atomicExch(status, kDevSingular);
       piv = DBL_MIN;
     }
-    la += log(fabs(piv));
+    la += log(absd(piv));
     if (piv < 0.0) sg = -sg;
     const double ipiv = 1.0 / piv;
     for (int jj = threadIdx.x; jj < n; jj += blockDim.x) {

@@ -345,8 +345,8 @@ __global__ void __launch_bounds__(256) k_drift_reset(const double* G64, T* Gw, i
   for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
     const double ge = g[e];
     bad |= !isfinite(ge);
-    md = fmax(md, fabs(static_cast<double>(w[e]) - ge));
-    mg = fmax(mg, fabs(ge));
+    md = fmax(md, absd(static_cast<double>(w[e]) - ge));
+    mg = fmax(mg, absd(ge));
     w[e] = static_cast<T>(ge);
   }
   __shared__ double s1[32], s2[32];
