@@ -292,6 +292,31 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_scan_ns(args):
+    """Drift of the working G at the stabilisation points against n_s, per
+    working precision (8 chains of the workload, 2 warm-up + 2 measured sweeps)."""
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    import numpy as np
+    for prec, nss in (("fp64", (10, 15, 20, 25, 30)), ("fp32", (2, 3, 5, 10))):
+        for ns in nss:
+            g = pkg.Group(Lx=W["Lx"], Ly=W["Ly"], t=W["t"], U=W["U"], beta=W["beta"],
+                          dtau=W["dtau"], n_chains=8, stab_interval=ns, delay_k=W["k"],
+                          precision=prec)
+            with pkg.DQMC([g], seed=0) as sim:
+                sim.sweep(2)
+                sim.reset_stats()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sim.sweep(2)
+                torch.cuda.synchronize()
+                dt = (time.perf_counter() - t0) / 2
+                d, _ = sim.stats()
+                print(json.dumps({"precision": prec, "n_s": ns, "drift_max": float(d.max()),
+                                  "drift_median": float(np.median(d)),
+                                  "s_per_sweep_8_chains": dt}), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -329,10 +354,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-workers", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--scan-ns", action="store_true",
+                    help="print the G drift against the stabilisation interval and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.scan_ns:
+        run_scan_ns(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
