@@ -175,6 +175,31 @@ int dqmc_timing_read(dqmc_ctx* ctx, double* ms, int64_t* launches, int n_classes
 int dqmc_timing_reset(dqmc_ctx* ctx);
 const char* dqmc_timing_class_name(int cls);
 
+/* Allocation-free entry point.  The paper has no counterpart: this exists for
+ * callers that may not allocate device memory (a process whose device memory
+ * belongs to another framework's allocator, a client under a hard memory
+ * quota, or a latency-critical loop that cannot absorb the device-wide
+ * synchronisation of cudaMalloc).  It computes the stabilised equal-time
+ * Green function of spin up, G = (I + B_L ... B_1)^{-1}, for ONE field
+ * configuration, exactly as dqmc_set_field + dqmc_get_G would, without any
+ * cudaMalloc/cudaFree: the intermediate matrices live in a fixed 4.2 MB
+ * device array inside libdqmc that every GPU loading the library holds until
+ * the process exits.
+ *   params: Lx, Ly, t, U, beta, dtau and stab_interval are used (validated as
+ *           for dqmc_init); n_chains, delay_k and precision are ignored.
+ *           Lx*Ly must not exceed DQMC_NOALLOC_MAX_N (else DQMC_ERR_ARG).
+ *   field:  device pointer, int8 [L][N] with values +-1 (caller-owned).
+ *   G_out:  device pointer, double [N][N] row-major (caller-owned).
+ *   stream: cudaStream_t or NULL; the call synchronises it before returning.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (other streams, other host threads) race and must be serialised.
+ * Returns DQMC_ERR_NAN if a pivot was singular or non-finite. */
+#define DQMC_NOALLOC_MAX_N 256
+int dqmc_green_noalloc(const dqmc_group* params, const int8_t* field, double* G_out,
+                       void* stream);
+
 void dqmc_destroy(dqmc_ctx* ctx);
 const char* dqmc_strerror(int code);
 

@@ -55,6 +55,8 @@ SIGNATURES = {
                                         ctypes.c_int]),
     "dqmc_timing_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_timing_class_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "dqmc_green_noalloc": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
     "dqmc_destroy": (None, [ctypes.c_void_p]),
     "dqmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
 }
