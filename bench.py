@@ -251,12 +251,21 @@ def run_ours(args):
         dist.init_process_group("nccl")
     seed = 1000 * rank  # independent chains per rank (weak scaling)
 
-    sim, gbuf, mixed = time_arm(pkg, torch, "fp32", args.steps, args.warmup, seed, dist)
+    # Mixed arm: float-pair (df32) Metropolis / delayed update / wrap on the FP32
+    # pipe with FP64 stabilisation -- the same G drift as plain FP64 (see
+    # --scan-ns).  Plain FP64 and FP32 working precision are timed beside it.
+    sim, gbuf, mixed = time_arm(pkg, torch, "df32", args.steps, args.warmup, seed, dist)
     prof = kernel_profile(sim, gbuf, args.steps, torch)
     e2e = e2e_arm(pkg, torch, sim, max(1, min(args.steps, 3)))
     sim.close()
-    sim64, gbuf64, plain = time_arm(pkg, torch, "fp64", args.steps, args.warmup, seed, dist)
-    sim64.close()
+    arms = {}
+    for prec in ("fp64", "fp32"):
+        s2, b2, res = time_arm(pkg, torch, prec, args.steps, args.warmup, seed, dist)
+        res["kernel_ms_per_step"] = {k: v[0] / args.steps
+                                     for k, v in kernel_profile(s2, b2, args.steps, torch).items()}
+        s2.close()
+        arms[prec] = res
+    plain = arms["fp64"]
 
     def slowest(ms):
         if not dist:
@@ -272,14 +281,19 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "fp32 Metropolis/delayed update/wrap, "
-                       "fp64 UDV/QR stabilisation, G recompute, drift, G(tau)",
+            "vs_baseline": None, "dtype": "df32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "df32 (float pairs) Metropolis/delayed "
+                       "update/wrap, fp64 UDV/QR stabilisation, G recompute, drift, G(tau)",
                        "chains_per_gpu": W["chains"], "L2": "working set > L2 (no flush needed)"},
             "drift": mixed["drift"], "acceptance": mixed["acceptance"],
             "fp64_plain": {"value": world * updates_per_sweep(W["chains"]) / (ms64 / 1e3),
                            "ms_per_step": ms64, "drift": plain["drift"],
-                           "speedup_mixed_over_fp64": ms64 / ms},
+                           "speedup_mixed_over_fp64": ms64 / ms,
+                           "kernel_ms_per_step": plain["kernel_ms_per_step"]},
+            "fp32_working": {"value": world * updates_per_sweep(W["chains"]) /
+                             (slowest(arms["fp32"]["ms"]) / 1e3),
+                             "ms_per_step": arms["fp32"]["ms"], "drift": arms["fp32"]["drift"],
+                             "kernel_ms_per_step": arms["fp32"]["kernel_ms_per_step"]},
             "roofline": roofline(prof, args.steps, fp64_peak()),
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "e2e": e2e, "gpu_launches": mixed["launches"], "clocks": mixed["clocks"],
@@ -298,7 +312,8 @@ def run_scan_ns(args):
     import torch
     import paper_1504_05090_gb300 as pkg
     import numpy as np
-    for prec, nss in (("fp64", (10, 15, 20, 25, 30)), ("fp32", (2, 3, 5, 10))):
+    for prec, nss in (("fp64", (10, 15, 20, 25, 30)), ("df32", (10, 15, 20, 25)),
+                      ("fp32", (2, 3, 5, 10))):
         for ns in nss:
             g = pkg.Group(Lx=W["Lx"], Ly=W["Ly"], t=W["t"], U=W["U"], beta=W["beta"],
                           dtau=W["dtau"], n_chains=8, stab_interval=ns, delay_k=W["k"],
@@ -315,6 +330,24 @@ def run_scan_ns(args):
                 print(json.dumps({"precision": prec, "n_s": ns, "drift_max": float(d.max()),
                                   "drift_median": float(np.median(d)),
                                   "s_per_sweep_8_chains": dt}), flush=True)
+
+
+def run_profile_case(args):
+    """Small case for ncu captures: the 16x16 kernels on 64 chains with L = 20
+    (beta = 2.5), one initialisation and one sweep with G(tau); about 0.4 GB."""
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    g = pkg.Group(Lx=W["Lx"], Ly=W["Ly"], t=W["t"], U=W["U"], beta=2.5, dtau=W["dtau"],
+                  n_chains=W["chains"], stab_interval=W["ns"], delay_k=W["k"],
+                  precision=args.precision)
+    with pkg.DQMC([g], seed=0) as sim:
+        buf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64,
+                          device="cuda")
+        step_device(sim, buf)
+        torch.cuda.synchronize()
+        d, a = sim.stats()
+        print(json.dumps({"profile_case": "16x16 L=20 64 chains", "drift": float(d.max()),
+                          "launches": sim.launch_count()}))
 
 
 def run_reference(args):
@@ -354,12 +387,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-workers", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run the small ncu capture case (16x16, L=20) and exit")
+    ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
     ap.add_argument("--scan-ns", action="store_true",
                     help="print the G drift against the stabilisation interval and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.scan_ns:
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.scan_ns:
         run_scan_ns(args)
     elif args.impl == "reference":
         run_reference(args)

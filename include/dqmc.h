@@ -55,6 +55,7 @@ extern "C" {
  * observables are FP64 in every mode. */
 #define DQMC_FP64 0
 #define DQMC_FP32 1
+#define DQMC_DF32 2 /* pairs of floats (hi + lo, ~48 bits) on the FP32 pipe */
 
 /* Limits of this build. */
 #define DQMC_MAX_SIDE 16  /* Lx, Ly <= 16, so N <= 256                          */
@@ -73,7 +74,7 @@ typedef struct {
     int32_t stab_interval; /* n_s >= 1: stabilise after every slice l with
                               l % n_s == 0 and after l = L                      */
     int32_t delay_k;       /* 1..DQMC_MAX_DELAY accepted flips per rank-k update */
-    int32_t precision;     /* DQMC_FP64 or DQMC_FP32                           */
+    int32_t precision;     /* DQMC_FP64, DQMC_FP32 or DQMC_DF32                */
 } dqmc_group;
 
 typedef struct dqmc_ctx dqmc_ctx; /* opaque, library-owned */

@@ -57,7 +57,7 @@ class Group:
         return n_slices(self.beta, self.dtau)
 
     def _c(self):
-        prec = {"fp64": _lib.DQMC_FP64, "fp32": _lib.DQMC_FP32}[self.precision]
+        prec = {"fp64": _lib.DQMC_FP64, "fp32": _lib.DQMC_FP32, "df32": _lib.DQMC_DF32}[self.precision]
         return _lib.DqmcGroup(self.Lx, self.Ly, self.t, self.U, self.beta, self.dtau,
                               self.n_chains, self.stab_interval, self.delay_k, prec)
 

@@ -14,6 +14,7 @@ LIB_PATH = os.path.join(HERE, "libdqmc.so")
 
 DQMC_FP64 = 0
 DQMC_FP32 = 1
+DQMC_DF32 = 2
 MAX_SIDE = 16
 MAX_DELAY = 32
 

@@ -79,6 +79,7 @@ struct Group {
   double *Mid = nullptr, *W1 = nullptr, *W2 = nullptr, *A1 = nullptr, *A2 = nullptr;
   double *logabs = nullptr, *obs = nullptr, *drift = nullptr, *bins = nullptr, *gacc = nullptr;
   double* gout = nullptr;  // [C][L+1][N] staging of G(tau) for host output
+  double* qrs = nullptr;   // [C][2N] column norms of the QR
   unsigned long long* acc = nullptr;
   int *d_cp_gtau = nullptr, *d_cp_grad = nullptr;
   long long nn() const { return static_cast<long long>(N) * N; }
@@ -215,6 +216,8 @@ KronArgs kron_base(const Group& g, int kind, int nv) {
   a.nv = nv;
   a.kind = kind;
   a.c = g.lam;  // sigma = +1 (spin up)
+  a.ec = std::exp(g.lam);
+  a.emc = std::exp(-g.lam);
   a.taps = g.taps;
   a.field = g.field;
   a.mat_stride = g.nn();
@@ -254,9 +257,9 @@ int stack_right(dqmc_ctx* ctx, Group& g, int j) {
   DQ_CLASS(ctx, kTStackKron);
   DQ_LAUNCH(ctx, launch_kron_rows<double>(g.RU + (j - 1) * g.nn(), g.X, g.C, a, ctx->st));
   DQ_CLASS(ctx, kTQR);
-  DQ_LAUNCH(ctx, launch_qrp(g.X, g.nn(), g.RU + j * g.nn(), g.sstride(), g.RD + j * g.N,
-                            static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.N, g.C,
-                            ctx->d_status, ctx->st));
+  DQ_LAUNCH(ctx, launch_qrp_cluster(g.X, g.nn(), g.RU + j * g.nn(), g.sstride(), g.RD + j * g.N,
+                                    static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.qrs,
+                                    g.N, g.C, ctx->d_status, ctx->st));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.B = g.RT + (j - 1) * g.nn(); m.sB = g.sstride();
@@ -279,9 +282,9 @@ int stack_left(dqmc_ctx* ctx, Group& g, int j) {
   DQ_CLASS(ctx, kTStackKron);
   DQ_LAUNCH(ctx, launch_kron_rows<double>(g.LU + (j + 1) * g.nn(), g.X, g.C, a, ctx->st));
   DQ_CLASS(ctx, kTQR);
-  DQ_LAUNCH(ctx, launch_qrp(g.X, g.nn(), g.LU + j * g.nn(), g.sstride(), g.LD + j * g.N,
-                            static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.N, g.C,
-                            ctx->d_status, ctx->st));
+  DQ_LAUNCH(ctx, launch_qrp_cluster(g.X, g.nn(), g.LU + j * g.nn(), g.sstride(), g.LD + j * g.N,
+                                    static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.qrs,
+                                    g.N, g.C, ctx->d_status, ctx->st));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.B = g.LT + (j + 1) * g.nn(); m.sB = g.sstride();
@@ -318,11 +321,12 @@ int form_mid(dqmc_ctx* ctx, Group& g, int j0, long long es, int batch, double* o
 int recompute(dqmc_ctx* ctx, Group& g, int j) {
   DQ_RET(form_mid(ctx, g, j, g.sstride(), g.C, g.X));
   DQ_CLASS(ctx, kTInverse);
-  DQ_LAUNCH(ctx, launch_gj_inverse(g.X, g.nn(), g.N, g.C, nullptr, nullptr, ctx->d_status, ctx->st));
+  DQ_LAUNCH(ctx, launch_gj_cluster(g.X, g.nn(), g.G64, g.nn(), g.N, g.C, nullptr, ctx->d_status,
+                                   ctx->st));
   GemmArgs m = gemm0(g.N);
   m.A = g.LU + j * g.nn(); m.sA = g.sstride(); m.tA = 1;
   m.ks = g.LD + j * g.N; m.sks = static_cast<long long>(g.nc + 1) * g.N; m.ks_mode = 2;
-  m.B = g.X; m.sB = g.nn();
+  m.B = g.G64; m.sB = g.nn();
   m.C = g.Rtil; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);
   DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
@@ -345,7 +349,22 @@ int drift_reset(dqmc_ctx* ctx, Group& g) {
 }
 
 int drift_reset_any(dqmc_ctx* ctx, Group& g) {
-  return g.p.precision == DQMC_FP32 ? drift_reset<float>(ctx, g) : drift_reset<double>(ctx, g);
+  if (g.p.precision == DQMC_FP32) return drift_reset<float>(ctx, g);
+  if (g.p.precision == DQMC_DF32) return drift_reset<df32>(ctx, g);
+  return drift_reset<double>(ctx, g);
+}
+
+// Working G <- stabilised G64 (no drift recorded).
+int load_working(dqmc_ctx* ctx, Group& g) {
+  ++ctx->launches;
+  cudaError_t e;
+  if (g.p.precision == DQMC_FP32)
+    e = launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), ctx->st);
+  else if (g.p.precision == DQMC_DF32)
+    e = launch_convert<df32>(g.G64, static_cast<df32*>(g.Gw), g.C * g.nn(), ctx->st);
+  else
+    e = launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st);
+  return e == cudaSuccess ? DQMC_OK : DQMC_ERR_CUDA;
 }
 
 int left_pass(dqmc_ctx* ctx, Group& g) {
@@ -422,6 +441,8 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
 int sweep_group(dqmc_ctx* ctx, Group& g, int measure) {
   if (g.p.precision == DQMC_FP32)
     DQ_RET(up_pass<float>(ctx, g, measure));
+  else if (g.p.precision == DQMC_DF32)
+    DQ_RET(up_pass<df32>(ctx, g, measure));
   else
     DQ_RET(up_pass<double>(ctx, g, measure));
   return left_pass(ctx, g);
@@ -437,17 +458,17 @@ int check_status(dqmc_ctx* ctx) {
 }
 
 // Stabilised matrices at all stabilisation points of every chain:
-// Mid^{-1} in g.Mid and W1 = U_L Db_L^{-1} Mid^{-1} in g.W1.
+// Mid^{-1} in g.A2 and W1 = U_L Db_L^{-1} Mid^{-1} in g.W1 (g.Mid is overwritten).
 int all_points_w1(dqmc_ctx* ctx, Group& g) {
   const int batch = g.C * (g.nc + 1);
   DQ_RET(form_mid(ctx, g, 0, g.nn(), batch, g.Mid));
   DQ_CLASS(ctx, kTInverse);
-  DQ_LAUNCH(ctx, launch_gj_inverse(g.Mid, g.nn(), g.N, batch, g.logabs, nullptr, ctx->d_status,
-                                   ctx->st));
+  DQ_LAUNCH(ctx, launch_gj_cluster(g.Mid, g.nn(), g.A2, g.nn(), g.N, batch, g.logabs,
+                                   ctx->d_status, ctx->st));
   GemmArgs m = gemm0(g.N);
   m.A = g.LU; m.sA = g.nn(); m.tA = 1;
   m.ks = g.LD; m.sks = g.N; m.ks_mode = 2;
-  m.B = g.Mid; m.sB = g.nn();
+  m.B = g.A2; m.sB = g.nn();
   m.C = g.W1; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);
   DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
@@ -463,7 +484,8 @@ int validate(const dqmc_group& p) {
   if (L < 1 || std::fabs(r - static_cast<double>(L)) > 1e-9 || L > 100000) return DQMC_ERR_ARG;
   if (p.n_chains < 1 || p.stab_interval < 1 || p.delay_k < 1 || p.delay_k > DQMC_MAX_DELAY)
     return DQMC_ERR_ARG;
-  if (p.precision != DQMC_FP64 && p.precision != DQMC_FP32) return DQMC_ERR_ARG;
+  if (p.precision != DQMC_FP64 && p.precision != DQMC_FP32 && p.precision != DQMC_DF32)
+    return DQMC_ERR_ARG;
   return DQMC_OK;
 }
 
@@ -483,7 +505,7 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
   ring_taps(p.Lx, p.t, p.dtau, g.taps.ex, g.taps.exi);
   ring_taps(p.Ly, p.t, p.dtau, g.taps.ey, g.taps.eyi);
   const size_t C = g.C, N = g.N, NN = N * N, S = static_cast<size_t>(g.nc + 1);
-  const size_t tsz = p.precision == DQMC_FP32 ? 4 : 8;
+  const size_t tsz = p.precision == DQMC_FP32 ? 4 : 8;  // df32 and double: 8 bytes
   DQ_RET(dev_alloc(ctx, &g.field, C * g.L * N));
   DQ_RET(dev_alloc(ctx, &g.Gw, C * NN * tsz));
   DQ_RET(dev_alloc(ctx, &g.G64, C * NN * 8));
@@ -507,6 +529,7 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
   DQ_RET(dev_alloc(ctx, &g.bins, C * (g.L + 1) * 2 * N * 8));
   DQ_RET(dev_alloc(ctx, &g.gacc, C * 3 * 8));
   DQ_RET(dev_alloc(ctx, &g.gout, C * (g.L + 1) * N * 8));
+  DQ_RET(dev_alloc(ctx, &g.qrs, C * 2 * N * 8));
   std::vector<int> cpg = g.cp, cpd = g.cp;
   cpg.push_back(g.L + 1);
   cpd.push_back(g.L);
@@ -582,15 +605,7 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
         rc = DQMC_ERR_CUDA;
     }
     if (rc == DQMC_OK) rc = rebuild(ctx, g);
-    if (rc == DQMC_OK) {
-      ++ctx->launches;
-      if (g.p.precision == DQMC_FP32)
-        rc = launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), ctx->st) ==
-                     cudaSuccess ? DQMC_OK : DQMC_ERR_CUDA;
-      else
-        rc = launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st) ==
-                     cudaSuccess ? DQMC_OK : DQMC_ERR_CUDA;
-    }
+    if (rc == DQMC_OK) rc = load_working(ctx, g);
   }
   ctx->total = chain0;
   if (rc == DQMC_OK) rc = check_status(ctx);
@@ -652,7 +667,7 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     m = gemm0(g.N);
     m.A = g.LT; m.sA = g.nn(); m.tA = 1;
     m.ks = g.LD; m.sks = g.N; m.ks_mode = 3;
-    m.B = g.Mid; m.sB = g.nn();
+    m.B = g.A2; m.sB = g.nn();
     m.C = g.W2; m.sC = g.nn();
     DQ_CLASS(ctx, kTGemm);
     DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
@@ -673,6 +688,8 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     ga.nv = kron_nv(g, true);
     ga.per_chain = g.nc + 1;
     ga.c = g.lam;
+    ga.ec = std::exp(g.lam);
+    ga.emc = std::exp(-g.lam);
     ga.taps = g.taps;
     ga.field = g.field;
     ga.cp = g.d_cp_gtau;
@@ -782,11 +799,7 @@ int dqmc_set_field(dqmc_ctx* ctx, const int8_t* in) {
     DQ_CK(cudaMemcpyAsync(g.field, in + off, n, cudaMemcpyHostToDevice, ctx->st));
     off += n;
     DQ_RET(rebuild(ctx, g));
-    ++ctx->launches;
-    if (g.p.precision == DQMC_FP32)
-      DQ_CK(launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), ctx->st));
-    else
-      DQ_CK(launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st));
+    DQ_RET(load_working(ctx, g));
   }
   return check_status(ctx);
 }

@@ -1,0 +1,465 @@
+// FP64 stabilisation kernels that spread one matrix over a thread-block
+// cluster of CS CTAs (one SM each), so that a batch of 64 matrices of order
+// 256 keeps 128 SMs busy instead of 64.  The matrices stay in global memory
+// (L2-resident: 512 KB each); each CTA updates the columns (QR) or rows
+// (Gauss-Jordan) it owns, and the CTAs meet at cluster barriers.  Within a
+// CTA every warp works on four columns at a time so that the FP64 pipe sees
+// independent dot products instead of one shuffle-reduction chain.
+//
+// Same mathematics as k_qrp / k_gj_inverse in k_linalg.cu (paper: the UDV
+// stabilisation behind Eq. (3) and G_ij(tau_l), Sec. 2).
+#include <cooperative_groups.h>
+
+#include <cfloat>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace dqmc {
+namespace {
+
+// Pivot search keys are compared in FP32: the choice of pivot only steers the
+// numerics (any pivot order gives an exact factorisation), and FP64 compares
+// cost a full pass of the 1/64-rate FP64 pipe on this part.
+struct AM {
+  float v;
+  int i;
+};
+
+__device__ __forceinline__ AM am_combine(AM a, AM b) {
+  return (b.v > a.v || (b.v == a.v && b.i < a.i)) ? b : a;
+}
+
+__device__ __forceinline__ AM warp_am(AM x) {
+  for (int o = 16; o > 0; o >>= 1) {
+    AM y;
+    y.v = __shfl_xor_sync(0xFFFFFFFFu, x.v, o);
+    y.i = __shfl_xor_sync(0xFFFFFFFFu, x.i, o);
+    x = am_combine(x, y);
+  }
+  return x;
+}
+
+// Block-wide argmax; every thread gets the winning index.
+__device__ int block_am(AM x, AM* sbuf, int* sres) {
+  x = warp_am(x);
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    AM y = (static_cast<int>(threadIdx.x) < nw) ? sbuf[threadIdx.x] : AM{-1.0f, 1 << 30};
+    y = warp_am(y);
+    if (threadIdx.x == 0) *sres = y.i;
+  }
+  __syncthreads();
+  return *sres;
+}
+
+__device__ __forceinline__ double wsum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v, double* sbuf) {
+  v = wsum(v);
+  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double y = (static_cast<int>(threadIdx.x) < static_cast<int>(blockDim.x >> 5)) ? sbuf[threadIdx.x] : 0.0;
+    y = wsum(y);
+    if (threadIdx.x == 0) sbuf[32] = y;
+  }
+  __syncthreads();
+  return sbuf[32];
+}
+
+// Apply I - tau v v^T (v = vsh[j..n), v_j = 1) to the rows M[c][j..n) for the
+// owned columns c = c0, c0 + CS, ... < n; four columns per warp at a time.
+// If vn1 != nullptr the partial column norms are downdated (column `pidx`
+// takes its input norm from position `jsrc`, see k_qrp_cluster).
+template <int CS>
+__device__ __forceinline__ void reflect_owned(double* M, int n, int j, int c0, double tau,
+                                              const double* vsh, double* vn1, double* vn2,
+                                              int pidx, int jsrc, double tol3z) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int m = (c0 < n) ? (n - c0 + CS - 1) / CS : 0;
+  for (int g = w; 4 * g < m; g += nw) {
+    int c[4];
+    bool ok[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ok[q] = (4 * g + q) < m;
+      c[q] = ok[q] ? c0 + CS * (4 * g + q) : c0;
+    }
+    // All rows of the four columns are loaded before any arithmetic, so each
+    // lane has up to 4 x kRPL independent loads in flight.
+    constexpr int kRPL = kMaxN / 32;
+    const int tmax = (n - j + 31) >> 5;  // warp-uniform: row slots that still hold live rows
+    double x[4][kRPL];
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) {
+      if (t < tmax) {
+        const int r = j + lane + 32 * t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          x[q][t] = (ok[q] && r < n) ? M[static_cast<size_t>(c[q]) * n + r] : 0.0;
+      }
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) {
+      if (t < tmax) {
+        const int r = j + lane + 32 * t;
+        const double vr = (r < n) ? vsh[r] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(vr, x[q][t], acc[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = wsum(acc[q]) * tau;
+    double top[4];
+#pragma unroll
+    for (int t = 0; t < kRPL; ++t) {
+      if (t < tmax) {
+        const int r = j + lane + 32 * t;
+        const double vr = (r < n) ? vsh[r] : 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          x[q][t] -= acc[q] * vr;
+          if (ok[q] && r < n) M[static_cast<size_t>(c[q]) * n + r] = x[q][t];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) top[q] = x[q][0];  // row j lives in lane 0, t = 0
+    if (vn1 == nullptr) continue;
+    // Downdate the partial norms (LAPACK xLAQP2); recompute on cancellation.
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (!ok[q]) continue;
+      const int src = (c[q] == pidx) ? jsrc : c[q];
+      const double n1 = vn1[src], n2 = vn2[src];
+      double nn1 = n1, nn2 = n2;
+      // The downdated norm only guides pivoting, so its ratio arithmetic runs
+      // in FP32 on one lane (an exact recomputation follows on cancellation).
+      int rec = 0;
+      if (lane == 0 && n1 != 0.0) {
+        float t = fabsf(static_cast<float>(top[q])) / static_cast<float>(n1);
+        t = fmaxf(0.0f, 1.0f - t * t);
+        const float qq = static_cast<float>(n1) / static_cast<float>(n2);
+        if (!(t * qq * qq > static_cast<float>(tol3z)))
+          rec = 1;
+        else
+          nn1 = n1 * static_cast<double>(sqrtf(t));
+      }
+      const bool recompute = __shfl_sync(0xFFFFFFFFu, rec, 0) != 0;
+      if (recompute) {
+        double s2 = 0.0;
+        for (int r = j + 1 + lane; r < n; r += 32) {
+          const double x = M[static_cast<size_t>(c[q]) * n + r];
+          s2 += x * x;
+        }
+        nn1 = sqrt(wsum(s2));
+        nn2 = nn1;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        vn1[c[q]] = nn1;
+        vn2[c[q]] = nn2;
+      }
+    }
+  }
+}
+
+// First column >= lo owned by cluster rank `rank` (ownership: c % CS == rank).
+template <int CS>
+__device__ __forceinline__ int first_owned(int lo, int rank) {
+  return lo + ((rank - lo % CS) % CS + CS) % CS;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Householder QR with column pivoting of X^T (row c = column c of X), one
+// cluster of CS CTAs per matrix.  Outputs as k_qrp: Q^T, D = |diag R| and
+// Rtil = D^{-1} R P^T.  Column norms live in Vn ([batch][2 n]).  The
+// Householder vectors are parked in the Rtil buffer until Q is formed.
+//
+// A column swap (j <-> p) moves the data of column j to position p without
+// touching the norm arrays: the owner of position p reads its input norm from
+// position j, which retires in the same step.  Two cluster barriers per step.
+// ---------------------------------------------------------------------------
+template <int CS>
+__global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX, double* Qall,
+                                                    long long sQ, double* Dall, long long sD,
+                                                    double* Rall, long long sR, double* Vn, int n,
+                                                    int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int b = blockIdx.x / CS;
+  double* X = Xall + b * sX;
+  double* Qt = Qall + b * sQ;
+  double* D = Dall + b * sD;
+  double* Rt = Rall + b * sR;
+  double* vn1 = Vn + static_cast<size_t>(b) * 2 * n;
+  double* vn2 = vn1 + n;
+  __shared__ double vsh[kMaxN], taus[kMaxN], betas[kMaxN];
+  __shared__ int perm[kMaxN];
+  __shared__ AM sred[32];
+  __shared__ int sres;
+  __shared__ double ssum[34];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double tol3z = 1.4901161193847656e-08;  // sqrt(DBL_EPSILON)
+
+  for (int c = rank + CS * w; c < n; c += CS * nw) {
+    double s = 0.0;
+    for (int r = lane; r < n; r += 32) {
+      const double x = X[static_cast<size_t>(c) * n + r];
+      s += x * x;
+    }
+    s = wsum(s);
+    if (lane == 0) {
+      vn1[c] = sqrt(s);
+      vn2[c] = vn1[c];
+    }
+  }
+  for (int c = threadIdx.x; c < n; c += blockDim.x) perm[c] = c;
+  cl.sync();
+
+  for (int j = 0; j < n; ++j) {
+    AM m{-1.0f, n};
+    for (int c = j + threadIdx.x; c < n; c += blockDim.x)
+      m = am_combine(m, AM{static_cast<float>(vn1[c]), c});
+    int p = block_am(m, sred, &sres);
+    if (p < j || p >= n) {
+      if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
+      p = j;
+    }
+    if (p != j) {
+      if (rank == 0) {
+        for (int r = threadIdx.x; r < n; r += blockDim.x) {
+          const double t = X[static_cast<size_t>(j) * n + r];
+          X[static_cast<size_t>(j) * n + r] = X[static_cast<size_t>(p) * n + r];
+          X[static_cast<size_t>(p) * n + r] = t;
+        }
+      }
+      if (threadIdx.x == 0) {
+        const int t = perm[j];
+        perm[j] = perm[p];
+        perm[p] = t;
+      }
+    }
+    cl.sync();
+    // Householder vector of column j (computed redundantly by every CTA).
+    const double* xj = X + static_cast<size_t>(j) * n;
+    double s = 0.0;
+    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) s += xj[r] * xj[r];
+    const double sig = block_sum(s, ssum);
+    if (threadIdx.x == 0) {  // reflector scalars: one thread, then broadcast
+      const double alpha = xj[j];
+      double tau = 0.0, beta = alpha, scal = 1.0;
+      if (sig != 0.0) {
+        const double nr = sqrt(alpha * alpha + sig);
+        beta = (alpha <= 0.0) ? nr : -nr;
+        tau = (beta - alpha) / beta;
+        scal = 1.0 / (alpha - beta);
+      }
+      taus[j] = tau;
+      betas[j] = beta;
+      ssum[33] = scal;
+    }
+    __syncthreads();
+    const double scal = ssum[33];
+    const double tau = taus[j];
+    for (int r = j + threadIdx.x; r < n; r += blockDim.x) {
+      const double v = (r == j) ? 1.0 : xj[r] * scal;
+      vsh[r] = v;
+      if (rank == 0 && r > j) Rt[static_cast<size_t>(j) * n + r] = v;
+    }
+    __syncthreads();
+    reflect_owned<CS>(X, n, j, first_owned<CS>(j + 1, rank), tau, vsh, vn1, vn2, p, j, tol3z);
+    cl.sync();
+  }
+
+  // Q = H_0 ... H_{n-1} accumulated backwards, owned columns (rows of Q^T).
+  for (int c = rank; c < n; c += CS)
+    for (int r = threadIdx.x; r < n; r += blockDim.x)
+      Qt[static_cast<size_t>(c) * n + r] = (c == r) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = n - 1; j >= 0; --j) {
+    for (int r = j + threadIdx.x; r < n; r += blockDim.x)
+      vsh[r] = (r == j) ? 1.0 : Rt[static_cast<size_t>(j) * n + r];
+    __syncthreads();
+    const double tau = taus[j];
+    if (tau != 0.0)
+      reflect_owned<CS>(Qt, n, j, first_owned<CS>(j, rank), tau, vsh, nullptr, nullptr, -1, -1,
+                        tol3z);
+    __syncthreads();
+  }
+  cl.sync();  // every CTA is done with the Householder vectors in Rt
+
+  // D = |beta|, Rtil[i][perm[c]] = R[i][c] / D[i], R[i][c] = X[c][i] (c > i), R[i][i] = beta_i.
+  for (int i = rank; i < n; i += CS) {
+    double d = absd(betas[i]);
+    if (!(d > 0.0)) {
+      if (threadIdx.x == 0) atomicExch(status, kDevSingular);
+      d = DBL_MIN;
+    }
+    if (threadIdx.x == 0) D[i] = d;
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      double v = 0.0;
+      if (c > i)
+        v = X[static_cast<size_t>(c) * n + i] / d;
+      else if (c == i)
+        v = betas[i] / d;
+      Rt[static_cast<size_t>(i) * n + perm[c]] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inverse, one cluster of CS CTAs per matrix, rows owned by
+// CTA (row % CS).  Pivot rows are chosen (partial pivoting over the rows not
+// yet used) but never moved; with pr[k] the pivot row of step k and ip its
+// inverse permutation, the in-place result Z gives A^{-1}[k][j] = Z[pr[k]][ip[j]],
+// written to Ainv at the end.  A is overwritten.  One cluster barrier per
+// step: the scaled pivot row is published by its owner one step late, after
+// the barrier, since no other CTA reads that row again.
+// ---------------------------------------------------------------------------
+template <int CS>
+__global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, double* Iall,
+                                                   long long sI, int n, double* logabs,
+                                                   int* status) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int b = blockIdx.x / CS;
+  double* A = Aall + b * sA;
+  double* Ainv = Iall + b * sI;
+  __shared__ double prow[kMaxN], pend[kMaxN];
+  __shared__ int pr[kMaxN], ip[kMaxN];
+  __shared__ unsigned char used[kMaxN];
+  __shared__ AM sred[32];
+  __shared__ int sres;
+  __shared__ double sinv;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
+  int pend_row = -1;  // owned pivot row whose scaled values wait in pend[]
+  double la = 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (pend_row >= 0) {
+      for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
+        A[static_cast<size_t>(pend_row) * n + jj] = pend[jj];
+      pend_row = -1;
+    }
+    AM m{-1.0f, n};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (!used[i]) m = am_combine(m, AM{static_cast<float>(absd(A[static_cast<size_t>(i) * n + k])), i});
+    int p = block_am(m, sred, &sres);
+    if (p < 0 || p >= n || used[p]) {  // no finite pivot left: flag, take the first free row
+      if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
+      p = 0;
+      while (p < n - 1 && used[p]) ++p;
+    }
+    if (threadIdx.x == 0) {  // pivot scalars: one thread, then broadcast
+      double piv = A[static_cast<size_t>(p) * n + k];
+      if (!(absd(piv) > 0.0)) {
+        atomicExch(status, kDevSingular);
+        piv = DBL_MIN;
+      }
+      la += log(absd(piv));
+      sinv = 1.0 / piv;
+    }
+    __syncthreads();
+    const double ipiv = sinv;
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
+      prow[jj] = (jj == k) ? ipiv : A[static_cast<size_t>(p) * n + jj] * ipiv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      used[p] = 1;
+      pr[k] = p;
+    }
+    // eliminate column k from the owned rows (the owned pivot row is only scaled)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int kRPL = kMaxN / 32;
+    const int tk = k >> 5, lk = k & 31;
+    for (int i0 = rank + CS * w; i0 < n; i0 += 2 * CS * nw) {
+      // two owned rows per warp and iteration, all their loads issued together
+      const int ii[2] = {i0, i0 + CS * nw};
+      double xv[2][kRPL];
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int t = 0; t < kRPL; ++t) {
+          const int jj = lane + 32 * t;
+          xv[h][t] = (ii[h] < n && jj < n) ? A[static_cast<size_t>(ii[h]) * n + jj] : 0.0;
+        }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = ii[h];
+        if (i >= n) continue;
+        double* Ai = A + static_cast<size_t>(i) * n;
+        if (i == p) {
+          for (int jj = lane; jj < n; jj += 32) pend[jj] = prow[jj];
+          continue;
+        }
+        double fk = 0.0;
+#pragma unroll
+        for (int t = 0; t < kRPL; ++t)
+          if (t == tk) fk = xv[h][t];
+        const double f = __shfl_sync(0xFFFFFFFFu, fk, lk);
+#pragma unroll
+        for (int t = 0; t < kRPL; ++t) {
+          const int jj = lane + 32 * t;
+          if (jj < n) Ai[jj] = (jj == k) ? -f * prow[k] : fma(-f, prow[jj], xv[h][t]);
+        }
+      }
+    }
+    if (p % CS == rank) pend_row = p;
+    cl.sync();
+  }
+  if (pend_row >= 0)
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
+      A[static_cast<size_t>(pend_row) * n + jj] = pend[jj];
+  __syncthreads();
+  for (int k = threadIdx.x; k < n; k += blockDim.x) ip[pr[k]] = k;
+  cl.sync();
+  for (int k = rank; k < n; k += CS) {
+    const double* Zr = A + static_cast<size_t>(pr[k]) * n;
+    for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
+      Ainv[static_cast<size_t>(k) * n + jj] = Zr[ip[jj]];
+  }
+  if (rank == 0 && threadIdx.x == 0 && logabs) logabs[b] = la;
+}
+
+template <typename K, typename... Args>
+static cudaError_t launch_cluster(K kern, int cs, int batch, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs * batch, 1, 1);
+  cfg.blockDim = dim3(512, 1, 1);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+cudaError_t launch_qrp_cluster(double* Xt, long long sX, double* Qt, long long sQ, double* D,
+                               long long sD, double* Rtil, long long sR, double* vnorm, int n,
+                               int batch, int* status, cudaStream_t st) {
+  return launch_cluster(k_qrp_cluster<2>, 2, batch, st, Xt, sX, Qt, sQ, D, sD, Rtil, sR, vnorm, n,
+                        status);
+}
+
+cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long sI, int n, int batch,
+                              double* logabs, int* status, cudaStream_t st) {
+  return launch_cluster(k_gj_cluster<2>, 2, batch, st, A, sA, Ainv, sI, n, logabs, status);
+}
+
+}  // namespace dqmc

@@ -43,9 +43,19 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmArgs a) {
   const double* cs = a.cs ? a.cs + b * a.scs : nullptr;
   __shared__ double As[16][64 + 2];
   __shared__ double Bs[16][64 + 2];
+  // Diagonal scale factors of this tile, formed once per tile (a division per
+  // loaded element would cost more FP64 issue than the tile's FMAs).
+  __shared__ double rsv[64], csv[64], ksv[16];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x < 64) {
+    const int i = i0 + threadIdx.x, jx = j0 + threadIdx.x;
+    rsv[threadIdx.x] = (i < n) ? a.alpha * scale_of(rs, a.rs_mode, i) : 0.0;
+    csv[threadIdx.x] = (jx < n) ? scale_of(cs, a.cs_mode, jx) : 0.0;
+  }
   double acc[4][4] = {};
   for (int k0 = 0; k0 < n; k0 += 16) {
+    if (threadIdx.x < 16) ksv[threadIdx.x] = (k0 + threadIdx.x < n) ? scale_of(ks, a.ks_mode, k0 + threadIdx.x) : 0.0;
+    __syncthreads();
     for (int e = threadIdx.x; e < 1024; e += 256) {
       int ii, kk;
       double v = 0.0;
@@ -58,8 +68,7 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmArgs a) {
         ii = e & 63;
         if (i0 + ii < n && k0 + kk < n) v = A[static_cast<size_t>(k0 + kk) * n + i0 + ii];
       }
-      if (k0 + kk < n) v *= scale_of(ks, a.ks_mode, k0 + kk);
-      As[kk][ii] = v;
+      As[kk][ii] = (a.ks_mode != 0) ? v * ksv[kk] : v;
       int jj;
       double w = 0.0;
       if (a.tB == 0) {
@@ -92,12 +101,12 @@ __global__ void __launch_bounds__(256) k_gemm_f64(GemmArgs a) {
   for (int r = 0; r < 4; ++r) {
     const int i = i0 + ty * 4 + r;
     if (i >= n) continue;
-    const double rsv = a.alpha * scale_of(rs, a.rs_mode, i);
+    const double rv = rsv[ty * 4 + r];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int j = j0 + tx * 4 + q;
       if (j >= n) continue;
-      double v = rsv * acc[r][q] * scale_of(cs, a.cs_mode, j);
+      double v = rv * acc[r][q] * csv[tx * 4 + q];
       const size_t o = static_cast<size_t>(i) * n + j;
       if (a.beta != 0.0) v += a.beta * C[o];
       C[o] = v;
@@ -415,8 +424,7 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
   for (int i = threadIdx.x; i < N; i += blockDim.x) sbin[i] = 0.0;
   const Geom g{a.Lx, a.Ly, N};
   const int8_t* f = a.field + static_cast<size_t>(chain) * a.L * N;
-  const double cexp = inv ? -a.c : a.c;
-  const double up = exp(cexp), dn = exp(-cexp);
+  const double up = inv ? a.emc : a.ec, dn = inv ? a.ec : a.emc;
   for (int l = lo; l < hi; ++l) {
     __syncthreads();
     if (l > lo) {
@@ -444,16 +452,22 @@ template <typename T>
 __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N, const T* tx,
                                  const T* ty, const T* pre, const T* post) {
   const int tot = nv * N;
+  if (pre) {  // diagonal factor applied once per element, not once per tap
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int vi = e / N, i = e - vi * N;
+      v[vi * ld + i] *= pre[i];
+    }
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int vi = e / N, i = e - vi * N;
     const int x = i % Lx, y = i / Lx;
     const T* row = v + vi * ld + Lx * y;
-    const T* pr = pre ? pre + Lx * y : nullptr;
     T acc = T(0);
     for (int xp = 0; xp < Lx; ++xp) {
       int dd = x - xp;
       dd += dd < 0 ? Lx : 0;
-      acc += tx[dd] * (pr ? row[xp] * pr[xp] : row[xp]);
+      acc = fma(tx[dd], row[xp], acc);
     }
     tmp[vi * ld + i] = acc;
   }
@@ -466,7 +480,7 @@ __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, i
     for (int yp = 0; yp < Ly; ++yp) {
       int dd = y - yp;
       dd += dd < 0 ? Ly : 0;
-      acc += ty[dd] * col[Lx * yp];
+      acc = fma(ty[dd], col[Lx * yp], acc);
     }
     v[vi * ld + i] = post ? acc * post[i] : acc;
   }
@@ -573,6 +587,7 @@ cudaError_t launch_convert(const double* src, T* dst, long long n, cudaStream_t 
 }
 template cudaError_t launch_convert<double>(const double*, double*, long long, cudaStream_t);
 template cudaError_t launch_convert<float>(const double*, float*, long long, cudaStream_t);
+template cudaError_t launch_convert<df32>(const double*, df32*, long long, cudaStream_t);
 
 cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, cudaStream_t st) {
   const size_t sm = (2ull * a.nv * (a.N + 1) + 2 * kMaxSide + 2ull * a.N) * sizeof(double);

@@ -49,12 +49,25 @@ __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int 
   T v[kMaxDelay];
 #pragma unroll
   for (int m = 0; m < kMaxDelay; ++m) v[m] = (m < cnt) ? V[m * NP + j] : T(0);
-  for (int r = 0; r < N; ++r) {
-    T acc = G[static_cast<size_t>(r) * N + j];
+  // Eight rows per iteration: their loads are issued together, so the L2
+  // latency is paid once per eight rows instead of once per row.
+  constexpr int RB = 8;
+  for (int r0 = 0; r0 < N; r0 += RB) {
+    T g[RB];
 #pragma unroll
-    for (int m = 0; m < kMaxDelay; ++m)
-      if (m < cnt) acc += U[m * NP + r] * v[m];
-    G[static_cast<size_t>(r) * N + j] = acc;
+    for (int q = 0; q < RB; ++q)
+      g[q] = (r0 + q < N) ? G[static_cast<size_t>(r0 + q) * N + j] : T(0);
+#pragma unroll
+    for (int m = 0; m < kMaxDelay; ++m) {
+      if (m < cnt) {
+#pragma unroll
+        for (int q = 0; q < RB; ++q)
+          if (r0 + q < N) g[q] += U[m * NP + r0 + q] * v[m];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      if (r0 + q < N) G[static_cast<size_t>(r0 + q) * N + j] = g[q];
   }
 }
 
@@ -87,36 +100,44 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
   }
   __syncthreads();
 
-  T colv = T(0), rowv = T(0);
-  if (act) {
-    colv = G[static_cast<size_t>(j) * N];
-    rowv = G[j];
+  // Column i and row i of G for the next kPre sites, loaded ahead (a flush
+  // rewrites G, after which the window is reloaded).
+  constexpr int kPre = 4;
+  T pc[kPre], pr[kPre];
+#pragma unroll
+  for (int q = 0; q < kPre; ++q) {
+    pc[q] = (act && q < N) ? G[static_cast<size_t>(j) * N + q] : T(0);
+    pr[q] = (act && q < N) ? G[static_cast<size_t>(q) * N + j] : T(0);
   }
   int cnt = 0;
   unsigned naccept = 0;
   for (int i = 0; i < N; ++i) {
-    T ncol = T(0), nrow = T(0);
-    if (act && i + 1 < N) {
-      ncol = G[static_cast<size_t>(j) * N + i + 1];
-      nrow = G[static_cast<size_t>(i + 1) * N + j];
+    const T colv = pc[0], rowv = pr[0];
+#pragma unroll
+    for (int q = 0; q + 1 < kPre; ++q) {
+      pc[q] = pc[q + 1];
+      pr[q] = pr[q + 1];
     }
+    const int inext = i + kPre;
+    pc[kPre - 1] = (act && inext < N) ? G[static_cast<size_t>(j) * N + inext] : T(0);
+    pr[kPre - 1] = (act && inext < N) ? G[static_cast<size_t>(inext) * N + j] : T(0);
     int acc_i = 0;
-    double ru = 1.0, du = 0.0;
-    if (lane == 0) {
+    double coefd = 0.0;
+    if (lane == 0) {  // ratio and coefficient on one lane per warp (FP64)
       const double g = static_cast<double>(d[i]);
       const int s = ss[i];
-      du = s > 0 ? a.em2 : a.ep2;
+      const double du = s > 0 ? a.em2 : a.ep2;
       const double dd = s > 0 ? a.ep2 : a.em2;
-      ru = 1.0 + du * (1.0 - g);
+      const double ru = 1.0 + du * (1.0 - g);
       const double rd = 1.0 + dd * g;
       acc_i = uu[i] < ru * rd;
+      if (acc_i) coefd = -du / ru;
     }
     acc_i = __shfl_sync(0xFFFFFFFFu, acc_i, 0);
     if (acc_i) {
-      du = __shfl_sync(0xFFFFFFFFu, du, 0);
-      ru = __shfl_sync(0xFFFFFFFFu, ru, 0);
+      coefd = __shfl_sync(0xFFFFFFFFu, coefd, 0);
       ++naccept;
-      const T coef = static_cast<T>(-du / ru);
+      const T coef = static_cast<T>(coefd);
       if (act) {
         T gc = colv, gr = rowv;
         for (int m = 0; m < cnt; ++m) {
@@ -139,14 +160,14 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
         delayed_flush(G, U, V, cnt, N, NP, j);
         cnt = 0;
         __syncthreads();
-        if (act && i + 1 < N) {
-          ncol = G[static_cast<size_t>(j) * N + i + 1];
-          nrow = G[static_cast<size_t>(i + 1) * N + j];
+#pragma unroll
+        for (int q = 0; q < kPre; ++q) {
+          const int ii = i + 1 + q;
+          pc[q] = (act && ii < N) ? G[static_cast<size_t>(j) * N + ii] : T(0);
+          pr[q] = (act && ii < N) ? G[static_cast<size_t>(ii) * N + j] : T(0);
         }
       }
     }
-    colv = ncol;
-    rowv = nrow;
   }
   if (cnt > 0) delayed_flush(G, U, V, cnt, N, NP, j);
   if (j == 0) a.accepted[c] += naccept;
@@ -161,24 +182,22 @@ __device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int
                                                const T* tx, const T* ty, const T* pre,
                                                const T* post) {
   const int tot = nv * N;
+  if (pre) {  // diagonal factor applied once per element, not once per tap
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+      const int vi = e / N, i = e - vi * N;
+      v[vi * ld + i] *= pre[i];
+    }
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int vi = e / N, i = e - vi * N;
     const int x = i % Lx, y = i / Lx;
     const T* row = v + vi * ld + Lx * y;
     T acc = T(0);
-    if (pre) {
-      const T* pr = pre + Lx * y;
-      for (int xp = 0; xp < Lx; ++xp) {
-        int dd = x - xp;
-        dd += dd < 0 ? Lx : 0;
-        acc += tx[dd] * (row[xp] * pr[xp]);
-      }
-    } else {
-      for (int xp = 0; xp < Lx; ++xp) {
-        int dd = x - xp;
-        dd += dd < 0 ? Lx : 0;
-        acc += tx[dd] * row[xp];
-      }
+    for (int xp = 0; xp < Lx; ++xp) {
+      int dd = x - xp;
+      dd += dd < 0 ? Lx : 0;
+      acc = madd(tx[dd], row[xp], acc);
     }
     tmp[vi * ld + i] = acc;
   }
@@ -191,7 +210,7 @@ __device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int
     for (int yp = 0; yp < Ly; ++yp) {
       int dd = y - yp;
       dd += dd < 0 ? Ly : 0;
-      acc += ty[dd] * col[Lx * yp];
+      acc = madd(ty[dd], col[Lx * yp], acc);
     }
     v[vi * ld + i] = post ? acc * post[i] : acc;
   }
@@ -248,8 +267,9 @@ __device__ __forceinline__ void kron_load_taps(const KronArgs& a, KronStage<T> s
 template <typename T>
 __device__ __forceinline__ void kron_load_scale(const KronArgs& a, KronStage<T> s,
                                                 const int8_t* f_l, int N) {
-  const double cexp = (a.kind == kBIT) ? -a.c : a.c;
-  const T up = static_cast<T>(exp(cexp)), dn = static_cast<T>(exp(-cexp));
+  // e^{+-c}, precomputed on the host: FP64 exp is dozens of FP64-pipe passes.
+  const T up = static_cast<T>((a.kind == kBIT) ? a.emc : a.ec);
+  const T dn = static_cast<T>((a.kind == kBIT) ? a.ec : a.emc);
   for (int i = threadIdx.x; i < N; i += blockDim.x) s.sc[i] = f_l[i] > 0 ? up : dn;
 }
 
@@ -500,6 +520,7 @@ cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double 
   template size_t metropolis_smem<T>(int, int);
 DQMC_INST(double)
 DQMC_INST(float)
+DQMC_INST(df32)
 #undef DQMC_INST
 
 }  // namespace dqmc

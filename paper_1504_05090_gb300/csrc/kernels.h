@@ -24,6 +24,7 @@ struct KronArgs {
   int nv;                // vectors per CTA
   int kind;              // KronKind
   double c;              // sigma * lambda
+  double ec, emc;        // exp(c), exp(-c), formed on the host
   KronTaps taps;
   const int8_t* field;   // [chain][L][N]
   long long mat_stride;  // elements between batch matrices (input / in place)
@@ -78,6 +79,14 @@ cudaError_t launch_qrp(double* Xt, long long sX, double* Qt, long long sQ, doubl
 // In-place Gauss-Jordan inverse with row pivoting; logabs/sign of det (may be null).
 cudaError_t launch_gj_inverse(double* A, long long sA, int n, int batch, double* logabs,
                               double* sign, int* status, cudaStream_t st);
+// Cluster variants (k_cluster.cu): one 2-CTA cluster per matrix.
+// QR: vnorm is scratch of 2 n doubles per matrix.
+cudaError_t launch_qrp_cluster(double* Xt, long long sX, double* Qt, long long sQ, double* D,
+                               long long sD, double* Rtil, long long sR, double* vnorm, int n,
+                               int batch, int* status, cudaStream_t st);
+// Gauss-Jordan: A (overwritten) -> Ainv, out of place; logabs may be null.
+cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long sI, int n, int batch,
+                              double* logabs, int* status, cudaStream_t st);
 cudaError_t launch_set_identity(double* M, long long sM, double* D, long long sD, int n, int batch,
                                 cudaStream_t st);
 template <typename T>
@@ -89,6 +98,7 @@ struct GtauArgs {
   int kind;              // kB for G(l,0)^T rows, kBIT for Y rows
   int vec_is_col;        // 1: vector q is column q of G(l,0); 0: vector q is row q of Y
   double c;
+  double ec, emc;        // exp(c), exp(-c)
   KronTaps taps;
   const int8_t* field;
   const int* cp;         // checkpoint slices, per_chain + 1 entries... (block b: cp[b]..cp[b+1])

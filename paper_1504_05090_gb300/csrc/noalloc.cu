@@ -129,6 +129,8 @@ extern "C" int dqmc_green_noalloc(const dqmc_group* p, const int8_t* field, doub
   a.L = L;
   a.kind = kB;
   a.c = std::acosh(std::exp(0.5 * p->dtau * p->U));
+  a.ec = std::exp(a.c);
+  a.emc = std::exp(-a.c);
   taps_1d(p->Lx, p->t, p->dtau, a.taps.ex, a.taps.exi);
   taps_1d(p->Ly, p->t, p->dtau, a.taps.ey, a.taps.eyi);
   a.field = field;

@@ -179,6 +179,24 @@ def test_autograd_function_backward():
         assert lam.grad.item() == pytest.approx(float(np.sum(dl * [1, 2, 3])), rel=1e-12)
 
 
+# -- df32 working precision (float pairs): FP64-class decisions ---------------
+@pytest.mark.parametrize("Lx,Ly,beta,dtau,ns,k", [(4, 4, 2.0, 0.125, 4, 4), (6, 6, 2.0, 0.1, 6, 8),
+                                                  (8, 8, 1.0, 0.125, 3, 16)])
+def test_df32_sweeps_match_oracle(Lx, Ly, beta, dtau, ns, k):
+    g = _grp(Lx, Ly, beta=beta, dtau=dtau, ns=ns, k=k, C=2, prec="df32")
+    p = _params(g)
+    with _sim([g], seed=11) as sim:
+        chains = [o.Chain(p, seed=11, chain=c) for c in range(2)]
+        for sweep in range(2):
+            sim.sweep(1, measure=True)
+            for c, ch in enumerate(chains):
+                out = ch.sweep()
+                assert np.array_equal(sim.field()[0][c], ch.field), (sweep, c)
+                assert _rel(sim.G(c, 0), out["G_up"]) < GTOL
+        drift, _ = sim.stats()
+        assert np.all(drift < 1e-9), drift
+
+
 # -- FP32 working precision ---------------------------------------------------
 def test_fp32_path_replay_and_drift():
     g32 = _grp(8, 8, beta=4.0, dtau=0.125, ns=8, k=16, C=2, prec="fp32")
