@@ -410,6 +410,10 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
   ma.sweep_ctr = ctx->d_sweep;
   ma.em2 = em2;
   ma.ep2 = ep2;
+  ma.em2h = static_cast<float>(em2);
+  ma.em2l = static_cast<float>(em2 - static_cast<double>(ma.em2h));
+  ma.ep2h = static_cast<float>(ep2);
+  ma.ep2l = static_cast<float>(ep2 - static_cast<double>(ma.ep2h));
   ma.accepted = g.acc;
   const bool fp64 = sizeof(T) == 8;
   KronArgs wl = kron_base(g, kB, kron_nv(g, fp64));

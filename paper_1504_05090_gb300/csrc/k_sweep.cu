@@ -42,6 +42,62 @@ __global__ void k_init_field(int8_t* field, int C, int L, int N, int chain0, uin
 // The accept/reject decision is taken in FP64 by lane 0 of every warp and
 // broadcast with a shuffle, so all threads agree without a barrier.
 // ---------------------------------------------------------------------------
+// Working-precision helpers.
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return static_cast<float>(x); }
+__device__ __forceinline__ float to_f32(df32 x) { return x.hi + x.lo; }
+__device__ __forceinline__ float shfl0(float x) { return __shfl_sync(0xFFFFFFFFu, x, 0); }
+__device__ __forceinline__ double shfl0(double x) { return __shfl_sync(0xFFFFFFFFu, x, 0); }
+__device__ __forceinline__ df32 shfl0(df32 x) { return df32(shfl0(x.hi), shfl0(x.lo)); }
+
+// Sum of products s = sum_m u_m v_m.  For df32 the products are accumulated
+// with one TwoSum per term into (hi, lo) and rounded once at the end (about
+// 12 FP32 instructions per term instead of 27 for an exact df32 multiply-add;
+// relative error ~ m 2^-48).
+template <typename T>
+struct ProdSum {
+  T s;
+  __device__ __forceinline__ ProdSum() : s(T(0)) {}
+  __device__ __forceinline__ void add(T u, T v) { s = madd(u, v, s); }
+  __device__ __forceinline__ T get() const { return s; }
+};
+template <>
+struct ProdSum<df32> {
+  float hi, lo;
+  __device__ __forceinline__ ProdSum() : hi(0.0f), lo(0.0f) {}
+  __device__ __forceinline__ void add(df32 u, df32 v) {
+    const float p = u.hi * v.hi;
+    float e = fmaf(u.hi, v.hi, -p);
+    e = fmaf(u.hi, v.lo, e);
+    e = fmaf(u.lo, v.hi, e);
+    const float t = hi + p;
+    const float bb = t - hi;
+    lo += ((hi - (t - bb)) + (p - bb)) + e;
+    hi = t;
+  }
+  __device__ __forceinline__ df32 get() const { return df_fast_two_sum(hi, lo); }
+};
+
+// Sherman-Morrison coefficient -Delta_up / R_up in the working precision:
+// FP32 for float, FP64 for double, and a float reciprocal refined by one
+// Newton step in df32 arithmetic for df32 (no FP64 instruction).
+__device__ __forceinline__ float sm_coef(const MetroArgs& a, int s, float g) {
+  const float du = s > 0 ? a.em2h : a.ep2h;
+  return -du / fmaf(du, 1.0f - g, 1.0f);
+}
+__device__ __forceinline__ double sm_coef(const MetroArgs& a, int s, double g) {
+  const double du = s > 0 ? a.em2 : a.ep2;
+  return -du / fma(du, 1.0 - g, 1.0);
+}
+__device__ __forceinline__ df32 sm_coef(const MetroArgs& a, int s, df32 g) {
+  const df32 du = s > 0 ? df32(a.em2h, a.em2l) : df32(a.ep2h, a.ep2l);
+  const df32 one(1.0f, 0.0f);
+  const df32 ru = one + du * (one - g);
+  const df32 y0(1.0f / ru.hi, 0.0f);
+  const df32 y = y0 + y0 * (one - ru * y0);
+  return -(du * y);
+}
+
 template <typename T>
 __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int cnt, int N, int NP,
                                               int j) {
@@ -49,25 +105,27 @@ __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int 
   T v[kMaxDelay];
 #pragma unroll
   for (int m = 0; m < kMaxDelay; ++m) v[m] = (m < cnt) ? V[m * NP + j] : T(0);
-  // Eight rows per iteration: their loads are issued together, so the L2
-  // latency is paid once per eight rows instead of once per row.
+  // Rows in batches of RB, the next batch loaded while the current one is
+  // computed, so two batches of L2 loads are in flight per thread.
   constexpr int RB = 8;
+  T cur[RB], nxt[RB];
+#pragma unroll
+  for (int q = 0; q < RB; ++q) cur[q] = (q < N) ? G[static_cast<size_t>(q) * N + j] : T(0);
   for (int r0 = 0; r0 < N; r0 += RB) {
-    T g[RB];
+    const int r1 = r0 + RB;
 #pragma unroll
     for (int q = 0; q < RB; ++q)
-      g[q] = (r0 + q < N) ? G[static_cast<size_t>(r0 + q) * N + j] : T(0);
+      nxt[q] = (r1 + q < N) ? G[static_cast<size_t>(r1 + q) * N + j] : T(0);
 #pragma unroll
-    for (int m = 0; m < kMaxDelay; ++m) {
-      if (m < cnt) {
+    for (int q = 0; q < RB; ++q) {
+      ProdSum<T> acc;
 #pragma unroll
-        for (int q = 0; q < RB; ++q)
-          if (r0 + q < N) g[q] += U[m * NP + r0 + q] * v[m];
-      }
+      for (int m = 0; m < kMaxDelay; ++m)
+        if (m < cnt) acc.add(U[m * NP + r0 + q], v[m]);
+      if (r0 + q < N) G[static_cast<size_t>(r0 + q) * N + j] = cur[q] + acc.get();
     }
 #pragma unroll
-    for (int q = 0; q < RB; ++q)
-      if (r0 + q < N) G[static_cast<size_t>(r0 + q) * N + j] = g[q];
+    for (int q = 0; q < RB; ++q) cur[q] = nxt[q];
   }
 }
 
@@ -84,19 +142,25 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
 
   extern __shared__ __align__(16) unsigned char sm_raw[];
   double* uu = reinterpret_cast<double*>(sm_raw);  // [NP] proposal uniforms
-  T* U = reinterpret_cast<T*>(uu + NP);             // [k][NP]
+  float* uuf = reinterpret_cast<float*>(uu + NP);   // [NP] the same, rounded to float
+  T* U = reinterpret_cast<T*>(uuf + NP);            // [k][NP]
   T* V = U + a.k * NP;                              // [k][NP]
   T* d = V + a.k * NP;                              // [NP] diag of G_cur
-  int* ss = reinterpret_cast<int*>(d + NP);         // [NP] field of the slice
+  float* df = reinterpret_cast<float*>(d + NP);     // [NP] diag of G_cur, rounded to float
+  int* ss = reinterpret_cast<int*>(df + NP);        // [NP] field of the slice
 
   const uint32_t sweep = *a.sweep_ctr;
   if (act) {
-    d[j] = G[static_cast<size_t>(j) * N + j];
+    const T gjj = G[static_cast<size_t>(j) * N + j];
+    d[j] = gjj;
+    df[j] = to_f32(gjj);
     ss[j] = s_l[j];
     const uint4 r = philox4x32_10(make_uint4(static_cast<uint32_t>(j + N * a.l0), sweep,
                                              static_cast<uint32_t>(a.chain0 + c), kTagProposal),
                                   a.key0, a.key1);
-    uu[j] = uniform53(r.x, r.y);
+    const double u = uniform53(r.x, r.y);
+    uu[j] = u;
+    uuf[j] = static_cast<float>(u);
   }
   __syncthreads();
 
@@ -121,38 +185,52 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
     const int inext = i + kPre;
     pc[kPre - 1] = (act && inext < N) ? G[static_cast<size_t>(j) * N + inext] : T(0);
     pr[kPre - 1] = (act && inext < N) ? G[static_cast<size_t>(inext) * N + j] : T(0);
+    // Decision u < R_up R_dn with R_up = 1 + D_up (1 - G_ii), R_dn = 1 + D_dn G_ii
+    // (G_dn,ii = 1 - G_up,ii).  Lane 0 of every warp takes it in FP32 unless u
+    // lies within 1e-4 of R, where it is retaken in FP64; all warps agree
+    // without a barrier.
     int acc_i = 0;
-    double coefd = 0.0;
-    if (lane == 0) {  // ratio and coefficient on one lane per warp (FP64)
-      const double g = static_cast<double>(d[i]);
+    T coef = T(0);
+    if (lane == 0) {
       const int s = ss[i];
-      const double du = s > 0 ? a.em2 : a.ep2;
-      const double dd = s > 0 ? a.ep2 : a.em2;
-      const double ru = 1.0 + du * (1.0 - g);
-      const double rd = 1.0 + dd * g;
-      acc_i = uu[i] < ru * rd;
-      if (acc_i) coefd = -du / ru;
+      const float gf = df[i];
+      const float duf = s > 0 ? a.em2h : a.ep2h, ddf = s > 0 ? a.ep2h : a.em2h;
+      const float Rf = fmaf(duf, 1.0f - gf, 1.0f) * fmaf(ddf, gf, 1.0f);
+      const float uf = uuf[i];
+      if (uf < Rf * 0.9999f) {
+        acc_i = 1;
+      } else if (!(uf > Rf * 1.0001f)) {
+        const double g = static_cast<double>(d[i]);
+        const double du = s > 0 ? a.em2 : a.ep2, dd = s > 0 ? a.ep2 : a.em2;
+        acc_i = uu[i] < fma(du, 1.0 - g, 1.0) * fma(dd, g, 1.0);
+      }
+      if (acc_i) coef = sm_coef(a, s, d[i]);
     }
     acc_i = __shfl_sync(0xFFFFFFFFu, acc_i, 0);
     if (acc_i) {
-      coefd = __shfl_sync(0xFFFFFFFFu, coefd, 0);
+      coef = shfl0(coef);
       ++naccept;
-      const T coef = static_cast<T>(coefd);
       if (act) {
-        T gc = colv, gr = rowv;
+        ProdSum<T> sc, sr;
         for (int m = 0; m < cnt; ++m) {
-          gc += U[m * NP + j] * V[m * NP + i];
-          gr += U[m * NP + i] * V[m * NP + j];
+          sc.add(U[m * NP + j], V[m * NP + i]);
+          sr.add(U[m * NP + i], V[m * NP + j]);
         }
+        const T gc = colv + sc.get(), gr = rowv + sr.get();
         const T uj = coef * ((j == i ? T(1) : T(0)) - gc);
         U[cnt * NP + j] = uj;
         V[cnt * NP + j] = gr;
-        // d[i] and ss[i] are read by slower warps for this same site; both are
-        // dead for the rest of the slice, so they are left untouched.
-        if (j != i)
-          d[j] += uj * gr;
-        else
+        // Only the diagonal of sites still to come (j > i) is updated.  Warps
+        // pass rejected sites without a barrier, so a slower warp may still be
+        // deciding an earlier site j <= i: its d[j], df[j] (dead for the rest
+        // of the slice) must keep the value every other warp decided with.
+        if (j > i) {
+          const T dj = d[j] + uj * gr;
+          d[j] = dj;
+          df[j] = to_f32(dj);
+        } else if (j == i) {
           s_l[i] = static_cast<int8_t>(-ss[i]);
+        }
       }
       __syncthreads();
       ++cnt;
@@ -456,8 +534,8 @@ cudaError_t launch_init_field(int8_t* field, int C, int L, int N, int chain0, ui
 template <typename T>
 size_t metropolis_smem(int N, int k) {
   const int NP = ((N + 31) / 32) * 32;
-  return static_cast<size_t>(NP) * sizeof(double) + 2ull * k * NP * sizeof(T) +
-         static_cast<size_t>(NP) * sizeof(T) + static_cast<size_t>(NP) * sizeof(int);
+  return static_cast<size_t>(NP) * (sizeof(double) + sizeof(float)) + 2ull * k * NP * sizeof(T) +
+         static_cast<size_t>(NP) * (sizeof(T) + sizeof(float) + sizeof(int));
 }
 
 template <typename T>

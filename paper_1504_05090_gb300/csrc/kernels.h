@@ -16,6 +16,7 @@ struct MetroArgs {
   uint32_t key0, key1;
   const uint32_t* sweep_ctr;  // device word: index of the running sweep
   double em2, ep2;            // exp(-2 lambda) - 1, exp(+2 lambda) - 1
+  float em2h, em2l, ep2h, ep2l;  // the same as float pairs (hi + lo)
   unsigned long long* accepted;
 };
 

@@ -197,6 +197,20 @@ def test_df32_sweeps_match_oracle(Lx, Ly, beta, dtau, ns, k):
         assert np.all(drift < 1e-9), drift
 
 
+@pytest.mark.parametrize("prec", ["df32", "fp64"])
+def test_drift_stays_small_with_eight_warps(prec):
+    """N = 256 runs 8 warps through the site loop without a barrier at rejected
+    sites; a warp that lags behind must decide with the same G_ii as the rest.
+    A shared-state race there shows up as an O(1) drift within a few sweeps."""
+    g = _grp(16, 16, U=2.0, beta=5.0, dtau=0.125, ns=10, k=32, C=8, prec=prec)
+    with _sim([g], seed=3) as sim:
+        for _ in range(5):
+            sim.reset_stats()
+            sim.sweep(1)
+            drift, _ = sim.stats()
+            assert np.all(drift < 1e-8), drift
+
+
 # -- FP32 working precision ---------------------------------------------------
 def test_fp32_path_replay_and_drift():
     g32 = _grp(8, 8, beta=4.0, dtau=0.125, ns=8, k=16, C=2, prec="fp32")
