@@ -164,6 +164,19 @@ int dqmc_num_chains(const dqmc_ctx* ctx);
  * created (for launch accounting). */
 int64_t dqmc_launch_count(const dqmc_ctx* ctx);
 
+/* Implementation of the FP64 matrix products of the stabilisation (UDV stack
+ * updates, the split-D Green-function formula, G(tau) at stabilisation
+ * points), N >= 64 only:
+ *   DQMC_GEMM_TENSOR (default): tcgen05 tensor cores, each FP64 row/column
+ *     cut into eight exponent-aligned 7-bit digits (BF16 operands, exact FP32
+ *     accumulation of digit products, FP64 recombination); agrees with FP64
+ *     products to rounding level.
+ *   DQMC_GEMM_FP64: the FP64 pipe.
+ * Smaller clusters always use the FP64 pipe.  Errors: DQMC_ERR_ARG. */
+#define DQMC_GEMM_TENSOR 0
+#define DQMC_GEMM_FP64 1
+int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode);
+
 /* Optional per-launch timing (library tracing).  While enabled, every kernel
  * launch is bracketed by a pair of CUDA events on the context's stream and its
  * device time is added to the class of the kernel (metropolis, wrap,
@@ -203,6 +216,10 @@ int dqmc_green_noalloc(const dqmc_group* params, const int8_t* field, double* G_
 
 void dqmc_destroy(dqmc_ctx* ctx);
 const char* dqmc_strerror(int code);
+/* Message of the last CUDA runtime error that made a call on this host thread
+ * return DQMC_ERR_CUDA ("no error" if none); *line (may be NULL) receives the
+ * library source line that saw it. */
+const char* dqmc_last_cuda_error(int* line);
 
 #ifdef __cplusplus
 }

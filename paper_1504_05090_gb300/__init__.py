@@ -85,7 +85,7 @@ class DQMC:
         h = ctypes.c_void_p()
         _lib.check(lib().dqmc_init(arr, len(self.groups), int(seed) & 0xFFFFFFFFFFFFFFFF,
                                    ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
-                   "dqmc_init")
+                   "dqmc_init", lib())
         self._h = h
         self.n_chains = lib().dqmc_num_chains(h)
 
@@ -108,61 +108,66 @@ class DQMC:
 
     # -- Monte Carlo --------------------------------------------------------
     def sweep(self, n=1, measure=True):
-        _lib.check(lib().dqmc_sweep(self._h, int(n), int(bool(measure))), "dqmc_sweep")
+        _lib.check(lib().dqmc_sweep(self._h, int(n), int(bool(measure))), "dqmc_sweep", lib())
 
     def recompute_G(self):
         out = np.zeros(self.n_chains)
-        _lib.check(lib().dqmc_recompute_G(self._h, _ptr(out)), "dqmc_recompute_G")
+        _lib.check(lib().dqmc_recompute_G(self._h, _ptr(out)), "dqmc_recompute_G", lib())
         return out
 
     # -- state --------------------------------------------------------------
     def field(self):
         out = np.empty(lib().dqmc_field_size(self._h), dtype=np.int8)
-        _lib.check(lib().dqmc_get_field(self._h, _ptr(out)), "dqmc_get_field")
+        _lib.check(lib().dqmc_get_field(self._h, _ptr(out)), "dqmc_get_field", lib())
         return self._split(out, lambda g: (g.n_chains, g.L, g.N))
 
     def set_field(self, fields):
         flat = np.concatenate([np.ascontiguousarray(f, dtype=np.int8).ravel() for f in fields])
-        _lib.check(lib().dqmc_set_field(self._h, _ptr(flat)), "dqmc_set_field")
+        _lib.check(lib().dqmc_set_field(self._h, _ptr(flat)), "dqmc_set_field", lib())
 
     def G(self, chain, spin=0):
         g = self._group_of(chain)
         out = np.empty((g.N, g.N))
-        _lib.check(lib().dqmc_get_G(self._h, int(chain), int(spin), _ptr(out)), "dqmc_get_G")
+        _lib.check(lib().dqmc_get_G(self._h, int(chain), int(spin), _ptr(out)), "dqmc_get_G", lib())
         return out
 
     def observables(self):
         out = np.empty((self.n_chains, 4))
-        _lib.check(lib().dqmc_get_observables(self._h, _ptr(out)), "dqmc_get_observables")
+        _lib.check(lib().dqmc_get_observables(self._h, _ptr(out)), "dqmc_get_observables", lib())
         return out
 
     def reset_observables(self):
-        _lib.check(lib().dqmc_reset_observables(self._h), "dqmc_reset_observables")
+        _lib.check(lib().dqmc_reset_observables(self._h), "dqmc_reset_observables", lib())
 
     def stats(self):
         drift = np.empty(self.n_chains)
         acc = np.empty(self.n_chains, dtype=np.uint64)
-        _lib.check(lib().dqmc_get_stats(self._h, _ptr(drift), _ptr(acc)), "dqmc_get_stats")
+        _lib.check(lib().dqmc_get_stats(self._h, _ptr(drift), _ptr(acc)), "dqmc_get_stats", lib())
         return drift, acc
 
     def reset_stats(self):
-        _lib.check(lib().dqmc_reset_stats(self._h), "dqmc_reset_stats")
+        _lib.check(lib().dqmc_reset_stats(self._h), "dqmc_reset_stats", lib())
 
     def launch_count(self):
         return int(lib().dqmc_launch_count(self._h))
 
+    def set_gemm_mode(self, mode):
+        """'tensor' (default, tcgen05 digit-sliced FP64 products) or 'fp64'."""
+        code = {"tensor": _lib.DQMC_GEMM_TENSOR, "fp64": _lib.DQMC_GEMM_FP64}[mode]
+        _lib.check(lib().dqmc_set_gemm_mode(self._h, code), "dqmc_set_gemm_mode", lib())
+
     def timing(self, on=True):
         """Enable/disable per-launch CUDA-event timing by kernel class."""
-        _lib.check(lib().dqmc_timing_enable(self._h, int(bool(on))), "dqmc_timing_enable")
+        _lib.check(lib().dqmc_timing_enable(self._h, int(bool(on))), "dqmc_timing_enable", lib())
 
     def timing_reset(self):
-        _lib.check(lib().dqmc_timing_reset(self._h), "dqmc_timing_reset")
+        _lib.check(lib().dqmc_timing_reset(self._h), "dqmc_timing_reset", lib())
 
     def timing_read(self):
         """{class name: (total ms, launches)} since the last reset."""
         ms = np.zeros(16)
         n = np.zeros(16, dtype=np.int64)
-        k = _lib.check(lib().dqmc_timing_read(self._h, _ptr(ms), _ptr(n), 16), "dqmc_timing_read")
+        k = _lib.check(lib().dqmc_timing_read(self._h, _ptr(ms), _ptr(n), 16), "dqmc_timing_read", lib())
         return {lib().dqmc_timing_class_name(c).decode(): (float(ms[c]), int(n[c]))
                 for c in range(k)}
 
@@ -174,10 +179,10 @@ class DQMC:
         n = int(lib().dqmc_gtau_size(self._h))
         if out is not None:
             assert out.is_cuda and out.numel() == n
-            _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(out), 1), "dqmc_measure_Gtau")
+            _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(out), 1), "dqmc_measure_Gtau", lib())
             return out
         host = np.empty(n)
-        _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(host), 0), "dqmc_measure_Gtau")
+        _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(host), 0), "dqmc_measure_Gtau", lib())
         return self._split(host, lambda g: (g.n_chains, g.L + 1, g.N))
 
     def grad(self):
@@ -185,11 +190,11 @@ class DQMC:
         dt = np.empty(self.n_chains)
         dl = np.empty(self.n_chains)
         lw = np.empty(self.n_chains)
-        _lib.check(lib().dqmc_grad(self._h, _ptr(dt), _ptr(dl), _ptr(lw), 0), "dqmc_grad")
+        _lib.check(lib().dqmc_grad(self._h, _ptr(dt), _ptr(dl), _ptr(lw), 0), "dqmc_grad", lib())
         return dt, dl, lw
 
     def grad_device(self, dt, dl, lw):
-        _lib.check(lib().dqmc_grad(self._h, _ptr(dt), _ptr(dl), _ptr(lw), 1), "dqmc_grad")
+        _lib.check(lib().dqmc_grad(self._h, _ptr(dt), _ptr(dl), _ptr(lw), 1), "dqmc_grad", lib())
 
     # -- helpers ------------------------------------------------------------
     def _group_of(self, chain):

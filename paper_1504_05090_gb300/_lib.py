@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libdqmc.so")
 DQMC_FP64 = 0
 DQMC_FP32 = 1
 DQMC_DF32 = 2
+DQMC_GEMM_TENSOR = 0
+DQMC_GEMM_FP64 = 1
 MAX_SIDE = 16
 MAX_DELAY = 32
 
@@ -51,6 +53,7 @@ SIGNATURES = {
     "dqmc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_num_chains": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "dqmc_set_gemm_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int]),
@@ -60,6 +63,7 @@ SIGNATURES = {
                                           ctypes.c_void_p, ctypes.c_void_p]),
     "dqmc_destroy": (None, [ctypes.c_void_p]),
     "dqmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "dqmc_last_cuda_error": (ctypes.c_char_p, [ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -81,7 +85,12 @@ def load(path=LIB_PATH):
     return lib
 
 
-def check(code, where):
+def check(code, where, lib=None):
     if code < 0:
-        raise DqmcError(code, where)
+        err = DqmcError(code, where)
+        if code == -2 and lib is not None:
+            line = ctypes.c_int(0)
+            msg = lib.dqmc_last_cuda_error(ctypes.byref(line)).decode()
+            err = DqmcError(code, "%s [%s at libdqmc line %d]" % (where, msg, line.value))
+        raise err
     return code

@@ -129,6 +129,6 @@ struct KronTaps {
 };
 
 // Error/status word written by device code (never trapped).
-enum DevStatus : int { kDevOk = 0, kDevBadArg = 1, kDevNonFinite = 2, kDevSingular = 3 };
+enum DevStatus : int { kDevOk = 0, kDevBadArg = 1, kDevNonFinite = 2, kDevSingular = 3, kDevTimeout = 4 };
 
 }  // namespace dqmc

@@ -80,6 +80,8 @@ struct Group {
   double *logabs = nullptr, *obs = nullptr, *drift = nullptr, *bins = nullptr, *gacc = nullptr;
   double* gout = nullptr;  // [C][L+1][N] staging of G(tau) for host output
   double* qrs = nullptr;   // [C][2N] column norms of the QR
+  void* oz = nullptr;      // digit slices of the tensor-core FP64 GEMM
+  int oz_batch = 0;
   unsigned long long* acc = nullptr;
   int *d_cp_gtau = nullptr, *d_cp_grad = nullptr;
   long long nn() const { return static_cast<long long>(N) * N; }
@@ -102,6 +104,7 @@ static const char* kTimingNames[kTNumClasses] = {
 struct dqmc_ctx {
   std::vector<Group> g;
   cudaStream_t st = nullptr;
+  int gemm_mode = DQMC_GEMM_TENSOR;
   // timing: event pairs recorded around launches while enabled
   bool timing = false;
   int tclass = kTMisc;
@@ -120,10 +123,19 @@ struct dqmc_ctx {
 
 namespace {
 
+constexpr int kOzakiMinN = 64;  // smaller matrices stay on the FP64 pipe
+
+thread_local cudaError_t g_last_cuda = cudaSuccess;  // last failing CUDA call (this thread)
+thread_local int g_last_line = 0;
+
 #define DQ_CK(call)                                 \
   do {                                              \
     cudaError_t e_ = (call);                        \
-    if (e_ != cudaSuccess) return DQMC_ERR_CUDA;    \
+    if (e_ != cudaSuccess) {                        \
+      g_last_cuda = e_;                             \
+      g_last_line = __LINE__;                       \
+      return DQMC_ERR_CUDA;                         \
+    }                                               \
   } while (0)
 #define DQ_RET(call)                 \
   do {                               \
@@ -242,6 +254,14 @@ GemmArgs gemm0(int n) {
   return a;
 }
 
+// FP64 products: on the tensor cores (digit-sliced, FP64-level accuracy) for
+// N >= kOzakiMinN unless the context asks for the FP64 pipe.
+cudaError_t gemm(dqmc_ctx* ctx, Group& g, const GemmArgs& m, int batch) {
+  if (ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz)
+    return launch_gemm_ozaki(m, batch, g.oz, g.oz_batch, ctx->d_status, ctx->st);
+  return launch_gemm(m, batch, ctx->st);
+}
+
 // ---- UDV stack steps ------------------------------------------------------
 
 // Right stack entry j from entry j-1 and slices cp[j-1]+1 .. cp[j].
@@ -265,7 +285,7 @@ int stack_right(dqmc_ctx* ctx, Group& g, int j) {
   m.B = g.RT + (j - 1) * g.nn(); m.sB = g.sstride();
   m.C = g.RT + j * g.nn(); m.sC = g.sstride();
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, g.C));
   return DQMC_OK;
 }
 
@@ -290,7 +310,7 @@ int stack_left(dqmc_ctx* ctx, Group& g, int j) {
   m.B = g.LT + (j + 1) * g.nn(); m.sB = g.sstride();
   m.C = g.LT + j * g.nn(); m.sC = g.sstride();
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, g.C));
   return DQMC_OK;
 }
 
@@ -306,14 +326,14 @@ int form_mid(dqmc_ctx* ctx, Group& g, int j0, long long es, int batch, double* o
   m.rs = g.RD + j0 * g.N; m.srs = dstride; m.rs_mode = 2;
   m.cs = g.LD + j0 * g.N; m.scs = dstride; m.cs_mode = 2;
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
   m.A = g.RT + j0 * g.nn();
   m.B = g.LT + j0 * g.nn();
   m.rs_mode = 3;
   m.cs_mode = 3;
   m.beta = 1.0;
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
   return DQMC_OK;
 }
 
@@ -329,14 +349,14 @@ int recompute(dqmc_ctx* ctx, Group& g, int j) {
   m.B = g.G64; m.sB = g.nn();
   m.C = g.Rtil; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, g.C));
   m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.ks = g.RD + j * g.N; m.sks = static_cast<long long>(g.nc + 1) * g.N; m.ks_mode = 2;
   m.B = g.RU + j * g.nn(); m.sB = g.sstride();
   m.C = g.G64; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, g.C, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, g.C));
   return DQMC_OK;
 }
 
@@ -364,7 +384,12 @@ int load_working(dqmc_ctx* ctx, Group& g) {
     e = launch_convert<df32>(g.G64, static_cast<df32*>(g.Gw), g.C * g.nn(), ctx->st);
   else
     e = launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st);
-  return e == cudaSuccess ? DQMC_OK : DQMC_ERR_CUDA;
+  if (e != cudaSuccess) {
+    g_last_cuda = e;
+    g_last_line = __LINE__;
+    return DQMC_ERR_CUDA;
+  }
+  return DQMC_OK;
 }
 
 int left_pass(dqmc_ctx* ctx, Group& g) {
@@ -456,7 +481,7 @@ int check_status(dqmc_ctx* ctx) {
   DQ_CK(cudaStreamSynchronize(ctx->st));
   int s = 0;
   DQ_CK(cudaMemcpy(&s, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (s == kDevNonFinite) return DQMC_ERR_NAN;
+  if (s == kDevTimeout) return DQMC_ERR_TIMEOUT;
   if (s != 0) return DQMC_ERR_NAN;
   return DQMC_OK;
 }
@@ -475,7 +500,7 @@ int all_points_w1(dqmc_ctx* ctx, Group& g) {
   m.B = g.A2; m.sB = g.nn();
   m.C = g.W1; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);
-  DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+  DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
   return DQMC_OK;
 }
 
@@ -534,6 +559,10 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
   DQ_RET(dev_alloc(ctx, &g.gacc, C * 3 * 8));
   DQ_RET(dev_alloc(ctx, &g.gout, C * (g.L + 1) * N * 8));
   DQ_RET(dev_alloc(ctx, &g.qrs, C * 2 * N * 8));
+  if (static_cast<int>(N) >= kOzakiMinN) {
+    g.oz_batch = static_cast<int>(std::min<size_t>(C * S, 256));
+    DQ_RET(dev_alloc(ctx, &g.oz, ozaki_scratch_bytes(static_cast<int>(N), g.oz_batch)));
+  }
   std::vector<int> cpg = g.cp, cpd = g.cp;
   cpg.push_back(g.L + 1);
   cpd.push_back(g.L);
@@ -552,6 +581,11 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
 }  // namespace
 
 extern "C" {
+
+const char* dqmc_last_cuda_error(int* line) {
+  if (line) *line = g_last_line;
+  return cudaGetErrorString(g_last_cuda);
+}
 
 const char* dqmc_strerror(int code) {
   switch (code) {
@@ -605,8 +639,12 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
     chain0 += g.C;
     if (rc == DQMC_OK) {
       ++ctx->launches;
-      if (launch_init_field(g.field, g.C, g.L, g.N, g.chain0, seed, ctx->st) != cudaSuccess)
+      const cudaError_t e = launch_init_field(g.field, g.C, g.L, g.N, g.chain0, seed, ctx->st);
+      if (e != cudaSuccess) {
+        g_last_cuda = e;
+        g_last_line = __LINE__;
         rc = DQMC_ERR_CUDA;
+      }
     }
     if (rc == DQMC_OK) rc = rebuild(ctx, g);
     if (rc == DQMC_OK) rc = load_working(ctx, g);
@@ -667,21 +705,21 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     m.B = g.W1; m.sB = g.nn(); m.tB = 1;
     m.C = g.A1; m.sC = g.nn();
     DQ_CLASS(ctx, kTGemm);
-    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
     m = gemm0(g.N);
     m.A = g.LT; m.sA = g.nn(); m.tA = 1;
     m.ks = g.LD; m.sks = g.N; m.ks_mode = 3;
     m.B = g.A2; m.sB = g.nn();
     m.C = g.W2; m.sC = g.nn();
     DQ_CLASS(ctx, kTGemm);
-    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
     m = gemm0(g.N);
     m.A = g.W2; m.sA = g.nn();
     m.ks = g.RD; m.sks = g.N; m.ks_mode = 2;
     m.B = g.RU; m.sB = g.nn();
     m.C = g.A2; m.sC = g.nn();
     DQ_CLASS(ctx, kTGemm);
-    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
     const long long nb = static_cast<long long>(g.C) * (g.L + 1) * 2 * g.N;
     DQ_CLASS(ctx, kTMisc);
     DQ_LAUNCH(ctx, (k_zero<<<static_cast<int>(std::min<long long>((nb + 255) / 256, 1024)), 256, 0,
@@ -734,7 +772,7 @@ int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda, double* lo
     m.B = g.RU; m.sB = g.nn();
     m.C = g.A1; m.sC = g.nn();
     DQ_CLASS(ctx, kTGemm);
-    DQ_LAUNCH(ctx, launch_gemm(m, batch, ctx->st));
+    DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
     DQ_CK(cudaMemsetAsync(g.gacc, 0, g.C * 3 * sizeof(double), ctx->st));
     int maxlen = 0;
     for (int j = 0; j < g.nc; ++j) maxlen = std::max(maxlen, g.cp[j + 1] - g.cp[j]);
@@ -877,6 +915,12 @@ int dqmc_reset_stats(dqmc_ctx* ctx) {
 int dqmc_num_chains(const dqmc_ctx* ctx) { return ctx ? ctx->total : DQMC_ERR_ARG; }
 
 int64_t dqmc_launch_count(const dqmc_ctx* ctx) { return ctx ? ctx->launches : DQMC_ERR_ARG; }
+
+int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode) {
+  if (!ctx || (mode != DQMC_GEMM_TENSOR && mode != DQMC_GEMM_FP64)) return DQMC_ERR_ARG;
+  ctx->gemm_mode = mode;
+  return DQMC_OK;
+}
 
 int dqmc_timing_enable(dqmc_ctx* ctx, int on) {
   if (!ctx) return DQMC_ERR_ARG;

@@ -271,26 +271,26 @@ __device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int
     const int vi = e / N, i = e - vi * N;
     const int x = i % Lx, y = i / Lx;
     const T* row = v + vi * ld + Lx * y;
-    T acc = T(0);
+    ProdSum<T> acc;
     for (int xp = 0; xp < Lx; ++xp) {
       int dd = x - xp;
       dd += dd < 0 ? Lx : 0;
-      acc = madd(tx[dd], row[xp], acc);
+      acc.add(tx[dd], row[xp]);
     }
-    tmp[vi * ld + i] = acc;
+    tmp[vi * ld + i] = acc.get();
   }
   __syncthreads();
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int vi = e / N, i = e - vi * N;
     const int x = i % Lx, y = i / Lx;
     const T* col = tmp + vi * ld + x;
-    T acc = T(0);
+    ProdSum<T> acc;
     for (int yp = 0; yp < Ly; ++yp) {
       int dd = y - yp;
       dd += dd < 0 ? Ly : 0;
-      acc = madd(ty[dd], col[Lx * yp], acc);
+      acc.add(ty[dd], col[Lx * yp]);
     }
-    v[vi * ld + i] = post ? acc * post[i] : acc;
+    v[vi * ld + i] = post ? acc.get() * post[i] : acc.get();
   }
   __syncthreads();
 }

@@ -72,6 +72,12 @@ cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double 
                                cudaStream_t st);
 
 cudaError_t launch_gemm(const GemmArgs& a, int batch, cudaStream_t st);
+// The same product on the tcgen05 tensor cores with FP64-level accuracy
+// (k_ozaki.cu); scratch of ozaki_scratch_bytes(n, max_batch) bytes, batches
+// processed max_batch matrices at a time.
+size_t ozaki_scratch_bytes(int n, int max_batch);
+cudaError_t launch_gemm_ozaki(const GemmArgs& a, int batch, void* scratch, int max_batch,
+                              int* status, cudaStream_t st);
 // Householder QR with column pivoting of X^T stored row-major (row c = column
 // c of X).  Outputs Q^T (row c = column c of Q), D = |diag R| and
 // Rtil = D^{-1} R P^T with X = Q diag(D) Rtil.  X is overwritten.

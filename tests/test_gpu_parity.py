@@ -211,6 +211,24 @@ def test_drift_stays_small_with_eight_warps(prec):
             assert np.all(drift < 1e-8), drift
 
 
+def test_tensor_core_fp64_products_match_fp64_pipe():
+    """Digit-sliced tcgen05 products (default for N >= 64) against the FP64
+    pipe on the same fields: G(0), G(tau) and the gradient agree to 1e-12."""
+    g = _grp(16, 16, U=2.0, beta=10.0, dtau=0.125, ns=10, C=2)
+    gs = _grp(6, 6, U=2.0, beta=2.0, dtau=0.1, ns=5, C=1)  # N = 36: always the FP64 pipe
+    with _sim([g, gs], seed=5) as a, _sim([g, gs], seed=5) as b:
+        b.set_gemm_mode("fp64")
+        a.recompute_G()
+        b.recompute_G()
+        for c in range(3):
+            assert _rel(a.G(c, 0), b.G(c, 0)) < 1e-12
+        ga, gb = a.gtau(), b.gtau()
+        for x, y in zip(ga, gb):
+            np.testing.assert_allclose(x, y, rtol=0, atol=1e-12 * np.max(np.abs(y)))
+        for x, y in zip(a.grad(), b.grad()):
+            np.testing.assert_allclose(x, y, rtol=1e-12)
+
+
 # -- FP32 working precision ---------------------------------------------------
 def test_fp32_path_replay_and_drift():
     g32 = _grp(8, 8, beta=4.0, dtau=0.125, ns=8, k=16, C=2, prec="fp32")
