@@ -350,6 +350,64 @@ def run_profile_case(args):
                           "launches": sim.launch_count()}))
 
 
+def config_groups(pkg, name, precision):
+    """Parameter sets of the other benchmark configurations."""
+    G = pkg.Group
+    if name == "c1":   # 4x4, U = 1, beta = 10, dtau = 0.25 (L = 40), 1 chain, n_s = 10
+        return [G(Lx=4, Ly=4, t=0.25, U=1.0, beta=10.0, dtau=0.25, n_chains=1, stab_interval=10,
+                  delay_k=8, precision=precision)]
+    if name == "c2":   # 8x8, U = 2, beta = 20, dtau in {0.4, 0.2, 0.1}, 256 chains each, k = 16, n_s = 8
+        return [G(Lx=8, Ly=8, t=0.25, U=2.0, beta=20.0, dtau=dt, n_chains=256, stab_interval=8,
+                  delay_k=16, precision=precision) for dt in (0.4, 0.2, 0.1)]
+    if name == "c4":   # uneven batch: six lattices x 32 chains, U / beta / dtau round robin
+        sides = (6, 8, 10, 12, 14, 16)
+        Us, betas, dts = (1.0, 2.0, 3.0), (10.0, 15.0, 20.0), (0.2, 0.125, 0.1)
+        return [G(Lx=L, Ly=L, t=0.25, U=Us[i % 3], beta=betas[i % 3], dtau=dts[i % 3], n_chains=32,
+                  stab_interval=10, delay_k=16, precision=precision) for i, L in enumerate(sides)]
+    if name == "c5":   # 8x8, U = 2, beta = 10, dtau = 0.125 (L = 80), 512 chains, FP64, gradients
+        return [G(Lx=8, Ly=8, t=0.25, U=2.0, beta=10.0, dtau=0.125, n_chains=512, stab_interval=10,
+                  delay_k=16, precision="fp64")]
+    raise ValueError(name)
+
+
+def run_config(args):
+    """One JSON line per precision for a secondary configuration: sweeps (with
+    G(tau) for c2/c4, with the gradient for c5) per second and updates/s."""
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    precs = ("fp64",) if args.config == "c5" else ("df32", "fp64", "fp32")
+    for prec in precs:
+        groups = config_groups(pkg, args.config, prec)
+        with pkg.DQMC(groups, seed=0) as sim:
+            n_up = sum(g.n_chains * g.N * g.L for g in groups)
+            gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
+            dt = torch.empty(sim.n_chains, dtype=torch.float64, device="cuda")
+            dl, lw = torch.empty_like(dt), torch.empty_like(dt)
+
+            def step():
+                sim.sweep(1, measure=True)
+                if args.config in ("c2", "c4"):
+                    sim.gtau(out=gbuf)
+                if args.config == "c5":
+                    sim.grad_device(dt, dl, lw)
+            for _ in range(args.warmup):
+                step()
+            sim.reset_stats()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            d, a = sim.stats()
+            print(json.dumps({"config": args.config, "precision": prec, "ms_per_step": ms,
+                              "updates_per_s": n_up / (ms / 1e3), "chains": sim.n_chains,
+                              "drift_max": float(d.max()),
+                              "acceptance": float(a.sum()) / (n_up * args.steps)}), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -387,6 +445,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-workers", type=int, default=0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--config", default="", choices=["", "c1", "c2", "c4", "c5"],
+                    help="time a secondary configuration instead of the headline workload")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu capture case (16x16, L=20) and exit")
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
@@ -395,7 +455,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_case:
+    if args.config:
+        run_config(args)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.scan_ns:
         run_scan_ns(args)

@@ -106,6 +106,12 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed,
  * synchronising call.  Errors: DQMC_ERR_ARG, DQMC_ERR_CUDA. */
 int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure);
 
+/* Sweeps are replayed as one CUDA graph per measure flag (captured at the
+ * first dqmc_sweep: one branch per group, the groups run concurrently); with
+ * on = 0, or while timing is enabled, kernels are launched one by one on the
+ * context's stream in group order.  Default on. */
+int dqmc_use_graphs(dqmc_ctx* ctx, int on);
+
 /* Rebuild both UDV stacks of every chain from its current field and replace
  * the working G by the stabilised G(0).  max_drift_out: host array [chains]
  * receiving max|G_working - G_fresh| / max|G_fresh| before the replacement,

@@ -151,6 +151,10 @@ class DQMC:
     def launch_count(self):
         return int(lib().dqmc_launch_count(self._h))
 
+    def use_graphs(self, on=True):
+        """Replay sweeps as captured CUDA graphs (default) or launch one by one."""
+        _lib.check(lib().dqmc_use_graphs(self._h, int(bool(on))), "dqmc_use_graphs", lib())
+
     def set_gemm_mode(self, mode):
         """'tensor' (default, tcgen05 digit-sliced FP64 products) or 'fp64'."""
         code = {"tensor": _lib.DQMC_GEMM_TENSOR, "fp64": _lib.DQMC_GEMM_FP64}[mode]

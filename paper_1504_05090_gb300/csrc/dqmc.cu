@@ -82,6 +82,9 @@ struct Group {
   double* qrs = nullptr;   // [C][2N] column norms of the QR
   void* oz = nullptr;      // digit slices of the tensor-core FP64 GEMM
   int oz_batch = 0;
+  cudaStream_t st = nullptr;   // stream this group's work is enqueued on
+  cudaStream_t cap = nullptr;  // the group's own stream (graph capture branches)
+  cudaEvent_t join = nullptr;
   unsigned long long* acc = nullptr;
   int *d_cp_gtau = nullptr, *d_cp_grad = nullptr;
   long long nn() const { return static_cast<long long>(N) * N; }
@@ -105,6 +108,13 @@ struct dqmc_ctx {
   std::vector<Group> g;
   cudaStream_t st = nullptr;
   int gemm_mode = DQMC_GEMM_TENSOR;
+  // CUDA graph of one sweep of all groups (index: measure flag), captured on
+  // cap_main with one forked branch per group, replayed on st.
+  bool use_graph = true;
+  cudaStream_t cap_main = nullptr;
+  cudaEvent_t fork = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  long long graph_launches[2] = {0, 0};
   // timing: event pairs recorded around launches while enabled
   bool timing = false;
   int tclass = kTMisc;
@@ -258,8 +268,8 @@ GemmArgs gemm0(int n) {
 // N >= kOzakiMinN unless the context asks for the FP64 pipe.
 cudaError_t gemm(dqmc_ctx* ctx, Group& g, const GemmArgs& m, int batch) {
   if (ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz)
-    return launch_gemm_ozaki(m, batch, g.oz, g.oz_batch, ctx->d_status, ctx->st);
-  return launch_gemm(m, batch, ctx->st);
+    return launch_gemm_ozaki(m, batch, g.oz, g.oz_batch, ctx->d_status, g.st);
+  return launch_gemm(m, batch, g.st);
 }
 
 // ---- UDV stack steps ------------------------------------------------------
@@ -275,11 +285,11 @@ int stack_right(dqmc_ctx* ctx, Group& g, int j) {
   a.dir = 1;
   a.n_slices = g.cp[j] - g.cp[j - 1];
   DQ_CLASS(ctx, kTStackKron);
-  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.RU + (j - 1) * g.nn(), g.X, g.C, a, ctx->st));
+  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.RU + (j - 1) * g.nn(), g.X, g.C, a, g.st));
   DQ_CLASS(ctx, kTQR);
   DQ_LAUNCH(ctx, launch_qrp_cluster(g.X, g.nn(), g.RU + j * g.nn(), g.sstride(), g.RD + j * g.N,
                                     static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.qrs,
-                                    g.N, g.C, ctx->d_status, ctx->st));
+                                    g.N, g.C, ctx->d_status, g.st));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.B = g.RT + (j - 1) * g.nn(); m.sB = g.sstride();
@@ -300,11 +310,11 @@ int stack_left(dqmc_ctx* ctx, Group& g, int j) {
   a.dir = -1;
   a.n_slices = g.cp[j + 1] - g.cp[j];
   DQ_CLASS(ctx, kTStackKron);
-  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.LU + (j + 1) * g.nn(), g.X, g.C, a, ctx->st));
+  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.LU + (j + 1) * g.nn(), g.X, g.C, a, g.st));
   DQ_CLASS(ctx, kTQR);
   DQ_LAUNCH(ctx, launch_qrp_cluster(g.X, g.nn(), g.LU + j * g.nn(), g.sstride(), g.LD + j * g.N,
                                     static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.qrs,
-                                    g.N, g.C, ctx->d_status, ctx->st));
+                                    g.N, g.C, ctx->d_status, g.st));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.B = g.LT + (j + 1) * g.nn(); m.sB = g.sstride();
@@ -342,7 +352,7 @@ int recompute(dqmc_ctx* ctx, Group& g, int j) {
   DQ_RET(form_mid(ctx, g, j, g.sstride(), g.C, g.X));
   DQ_CLASS(ctx, kTInverse);
   DQ_LAUNCH(ctx, launch_gj_cluster(g.X, g.nn(), g.G64, g.nn(), g.N, g.C, nullptr, ctx->d_status,
-                                   ctx->st));
+                                   g.st));
   GemmArgs m = gemm0(g.N);
   m.A = g.LU + j * g.nn(); m.sA = g.sstride(); m.tA = 1;
   m.ks = g.LD + j * g.N; m.sks = static_cast<long long>(g.nc + 1) * g.N; m.ks_mode = 2;
@@ -364,7 +374,7 @@ template <typename T>
 int drift_reset(dqmc_ctx* ctx, Group& g) {
   DQ_CLASS(ctx, kTMisc);
   DQ_LAUNCH(ctx, launch_drift_reset<T>(g.G64, static_cast<T*>(g.Gw), g.C, g.N, g.drift,
-                                        ctx->d_status, ctx->st));
+                                        ctx->d_status, g.st));
   return DQMC_OK;
 }
 
@@ -379,11 +389,11 @@ int load_working(dqmc_ctx* ctx, Group& g) {
   ++ctx->launches;
   cudaError_t e;
   if (g.p.precision == DQMC_FP32)
-    e = launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), ctx->st);
+    e = launch_convert<float>(g.G64, static_cast<float*>(g.Gw), g.C * g.nn(), g.st);
   else if (g.p.precision == DQMC_DF32)
-    e = launch_convert<df32>(g.G64, static_cast<df32*>(g.Gw), g.C * g.nn(), ctx->st);
+    e = launch_convert<df32>(g.G64, static_cast<df32*>(g.Gw), g.C * g.nn(), g.st);
   else
-    e = launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), ctx->st);
+    e = launch_convert<double>(g.G64, static_cast<double*>(g.Gw), g.C * g.nn(), g.st);
   if (e != cudaSuccess) {
     g_last_cuda = e;
     g_last_line = __LINE__;
@@ -407,15 +417,15 @@ int right_pass(dqmc_ctx* ctx, Group& g) {
 int rebuild(dqmc_ctx* ctx, Group& g) {
   DQ_CLASS(ctx, kTMisc);
   DQ_LAUNCH(ctx, launch_set_identity(g.RU, g.sstride(), g.RD, static_cast<long long>(g.nc + 1) * g.N,
-                                     g.N, g.C, ctx->st));
+                                     g.N, g.C, g.st));
   DQ_CLASS(ctx, kTMisc);
-  DQ_LAUNCH(ctx, launch_set_identity(g.RT, g.sstride(), nullptr, 0, g.N, g.C, ctx->st));
+  DQ_LAUNCH(ctx, launch_set_identity(g.RT, g.sstride(), nullptr, 0, g.N, g.C, g.st));
   DQ_CLASS(ctx, kTMisc);
   DQ_LAUNCH(ctx, launch_set_identity(g.LU + g.nc * g.nn(), g.sstride(), g.LD + g.nc * g.N,
-                                     static_cast<long long>(g.nc + 1) * g.N, g.N, g.C, ctx->st));
+                                     static_cast<long long>(g.nc + 1) * g.N, g.N, g.C, g.st));
   DQ_CLASS(ctx, kTMisc);
   DQ_LAUNCH(ctx, launch_set_identity(g.LT + g.nc * g.nn(), g.sstride(), nullptr, 0, g.N, g.C,
-                                     ctx->st));
+                                     g.st));
   DQ_RET(right_pass(ctx, g));
   DQ_RET(left_pass(ctx, g));
   DQ_RET(recompute(ctx, g, 0));
@@ -449,18 +459,18 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
   for (int l = 1; l <= g.L; ++l) {
     ma.l0 = l - 1;
     DQ_CLASS(ctx, kTMetropolis);
-    DQ_LAUNCH(ctx, launch_metropolis<T>(Gw, g.field, g.C, ma, ctx->st));
+    DQ_LAUNCH(ctx, launch_metropolis<T>(Gw, g.field, g.C, ma, g.st));
     wl.l0_first = wr.l0_first = l - 1;
     DQ_CLASS(ctx, kTWrap);
-    DQ_LAUNCH(ctx, launch_kron_cols<T>(Gw, g.C, wl, ctx->st));
+    DQ_LAUNCH(ctx, launch_kron_cols<T>(Gw, g.C, wl, g.st));
     DQ_CLASS(ctx, kTWrap);
-    DQ_LAUNCH(ctx, launch_kron_rows<T>(Gw, Gw, g.C, wr, ctx->st));
+    DQ_LAUNCH(ctx, launch_kron_rows<T>(Gw, Gw, g.C, wr, g.st));
     if (l == g.cp[j]) {
       DQ_RET(stack_right(ctx, g, j));
       DQ_RET(recompute(ctx, g, j));
       DQ_RET(drift_reset<T>(ctx, g));
       if (measure)
-        DQ_LAUNCH_C(ctx, kTMisc, launch_observables(g.G64, g.C, g.p.Lx, g.p.Ly, g.p.t, g.obs, ctx->st));
+        DQ_LAUNCH_C(ctx, kTMisc, launch_observables(g.G64, g.C, g.p.Lx, g.p.Ly, g.p.t, g.obs, g.st));
       ++j;
     }
   }
@@ -493,7 +503,7 @@ int all_points_w1(dqmc_ctx* ctx, Group& g) {
   DQ_RET(form_mid(ctx, g, 0, g.nn(), batch, g.Mid));
   DQ_CLASS(ctx, kTInverse);
   DQ_LAUNCH(ctx, launch_gj_cluster(g.Mid, g.nn(), g.A2, g.nn(), g.N, batch, g.logabs,
-                                   ctx->d_status, ctx->st));
+                                   ctx->d_status, g.st));
   GemmArgs m = gemm0(g.N);
   m.A = g.LU; m.sA = g.nn(); m.tA = 1;
   m.ks = g.LD; m.sks = g.N; m.ks_mode = 2;
@@ -502,6 +512,61 @@ int all_points_w1(dqmc_ctx* ctx, Group& g) {
   DQ_CLASS(ctx, kTGemm);
   DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
   return DQMC_OK;
+}
+
+void drop_graphs(dqmc_ctx* ctx) {
+  for (int m = 0; m < 2; ++m) {
+    if (ctx->gexec[m]) cudaGraphExecDestroy(ctx->gexec[m]);
+    ctx->gexec[m] = nullptr;
+  }
+}
+
+// Capture one sweep of every group (each on its own branch, forked from and
+// joined into cap_main) followed by the sweep-counter increment.
+int build_sweep_graph(dqmc_ctx* ctx, int m) {
+  DQ_CK(cudaStreamBeginCapture(ctx->cap_main, cudaStreamCaptureModeRelaxed));
+  const long long l0 = ctx->launches;
+  int rc = DQMC_OK;
+  if (cudaEventRecord(ctx->fork, ctx->cap_main) != cudaSuccess) rc = DQMC_ERR_CUDA;
+  for (Group& g : ctx->g) {
+    if (rc != DQMC_OK) break;
+    if (cudaStreamWaitEvent(g.cap, ctx->fork, 0) != cudaSuccess) {
+      rc = DQMC_ERR_CUDA;
+      break;
+    }
+    g.st = g.cap;
+    rc = sweep_group(ctx, g, m);
+    g.st = ctx->st;
+    if (rc == DQMC_OK && (cudaEventRecord(g.join, g.cap) != cudaSuccess ||
+                          cudaStreamWaitEvent(ctx->cap_main, g.join, 0) != cudaSuccess))
+      rc = DQMC_ERR_CUDA;
+  }
+  if (rc == DQMC_OK) {
+    ++ctx->launches;
+    k_increment<<<1, 1, 0, ctx->cap_main>>>(ctx->d_sweep);
+    if (cudaGetLastError() != cudaSuccess) rc = DQMC_ERR_CUDA;
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(ctx->cap_main, &graph);
+  for (Group& g : ctx->g) g.st = ctx->st;
+  if (rc == DQMC_OK && ec != cudaSuccess) {
+    g_last_cuda = ec;
+    g_last_line = __LINE__;
+    rc = DQMC_ERR_CUDA;
+  }
+  if (rc == DQMC_OK) {
+    const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec[m], graph, 0);
+    if (ei != cudaSuccess) {
+      g_last_cuda = ei;
+      g_last_line = __LINE__;
+      ctx->gexec[m] = nullptr;
+      rc = DQMC_ERR_CUDA;
+    }
+  }
+  if (graph) cudaGraphDestroy(graph);
+  ctx->graph_launches[m] = ctx->launches - l0;
+  ctx->launches = l0;
+  return rc;
 }
 
 int validate(const dqmc_group& p) {
@@ -604,6 +669,14 @@ const char* dqmc_strerror(int code) {
 void dqmc_destroy(dqmc_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  cudaDeviceSynchronize();
+  drop_graphs(ctx);
+  for (Group& g : ctx->g) {
+    if (g.cap) cudaStreamDestroy(g.cap);
+    if (g.join) cudaEventDestroy(g.join);
+  }
+  if (ctx->cap_main) cudaStreamDestroy(ctx->cap_main);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
   for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   for (void* p : ctx->allocs) cudaFree(p);
   delete ctx;
@@ -635,6 +708,7 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
     Group& g = ctx->g[i];
     g.p = groups[i];
     g.chain0 = chain0;
+    g.st = ctx->st;
     rc = setup_group(ctx, g);
     chain0 += g.C;
     if (rc == DQMC_OK) {
@@ -650,6 +724,17 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
     if (rc == DQMC_OK) rc = load_working(ctx, g);
   }
   ctx->total = chain0;
+  if (rc == DQMC_OK) {
+    if (cudaStreamCreateWithFlags(&ctx->cap_main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming) != cudaSuccess)
+      rc = DQMC_ERR_CUDA;
+    for (Group& g : ctx->g) {
+      g.st = ctx->st;
+      if (rc == DQMC_OK && (cudaStreamCreateWithFlags(&g.cap, cudaStreamNonBlocking) != cudaSuccess ||
+                            cudaEventCreateWithFlags(&g.join, cudaEventDisableTiming) != cudaSuccess))
+        rc = DQMC_ERR_CUDA;
+    }
+  }
   if (rc == DQMC_OK) rc = check_status(ctx);
   if (rc != DQMC_OK) {
     dqmc_destroy(ctx);
@@ -661,11 +746,26 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
 
 int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure) {
   if (!ctx || n_sweeps < 0) return DQMC_ERR_ARG;
-  for (int s = 0; s < n_sweeps; ++s) {
-    for (Group& g : ctx->g) DQ_RET(sweep_group(ctx, g, measure));
-    DQ_CLASS(ctx, kTMisc);
-    DQ_LAUNCH(ctx, (k_increment<<<1, 1, 0, ctx->st>>>(ctx->d_sweep), cudaGetLastError()));
+  const int m = measure ? 1 : 0;
+  if (ctx->timing || !ctx->use_graph) {
+    for (int s = 0; s < n_sweeps; ++s) {
+      for (Group& g : ctx->g) DQ_RET(sweep_group(ctx, g, m));
+      DQ_CLASS(ctx, kTMisc);
+      DQ_LAUNCH(ctx, (k_increment<<<1, 1, 0, ctx->st>>>(ctx->d_sweep), cudaGetLastError()));
+    }
+    return DQMC_OK;
   }
+  if (n_sweeps > 0 && !ctx->gexec[m]) DQ_RET(build_sweep_graph(ctx, m));
+  for (int s = 0; s < n_sweeps; ++s) {
+    DQ_CK(cudaGraphLaunch(ctx->gexec[m], ctx->st));
+    ctx->launches += ctx->graph_launches[m];
+  }
+  return DQMC_OK;
+}
+
+int dqmc_use_graphs(dqmc_ctx* ctx, int on) {
+  if (!ctx) return DQMC_ERR_ARG;
+  ctx->use_graph = on != 0;
   return DQMC_OK;
 }
 
@@ -723,7 +823,7 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     const long long nb = static_cast<long long>(g.C) * (g.L + 1) * 2 * g.N;
     DQ_CLASS(ctx, kTMisc);
     DQ_LAUNCH(ctx, (k_zero<<<static_cast<int>(std::min<long long>((nb + 255) / 256, 1024)), 256, 0,
-                             ctx->st>>>(g.bins, nb),
+                             g.st>>>(g.bins, nb),
                     cudaGetLastError()));
     GtauArgs ga{};
     ga.N = g.N; ga.Lx = g.p.Lx; ga.Ly = g.p.Ly; ga.L = g.L;
@@ -739,18 +839,18 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     ga.bins = g.bins;
     ga.kind = kB; ga.vec_is_col = 1; ga.bin_slot = 0;
     DQ_CLASS(ctx, kTGtauProp);
-    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A1, batch, ga, ctx->st));
+    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A1, batch, ga, g.st));
     ga.kind = kBIT; ga.vec_is_col = 0; ga.bin_slot = 1;
     DQ_CLASS(ctx, kTGtauProp);
-    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, ctx->st));
+    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, g.st));
     const size_t cnt = static_cast<size_t>(g.C) * (g.L + 1) * g.N;
     if (out_on_device) {
       DQ_CLASS(ctx, kTGtauFinal);
-      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, out + off, g.C, g.L, g.p.Lx, g.p.Ly, ctx->st));
+      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, out + off, g.C, g.L, g.p.Lx, g.p.Ly, g.st));
     } else {
       DQ_CLASS(ctx, kTGtauFinal);
-      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, g.gout, g.C, g.L, g.p.Lx, g.p.Ly, ctx->st));
-      DQ_CK(cudaMemcpyAsync(out + off, g.gout, cnt * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, g.gout, g.C, g.L, g.p.Lx, g.p.Ly, g.st));
+      DQ_CK(cudaMemcpyAsync(out + off, g.gout, cnt * sizeof(double), cudaMemcpyDeviceToHost, g.st));
     }
     off += cnt;
   }
@@ -773,7 +873,7 @@ int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda, double* lo
     m.C = g.A1; m.sC = g.nn();
     DQ_CLASS(ctx, kTGemm);
     DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
-    DQ_CK(cudaMemsetAsync(g.gacc, 0, g.C * 3 * sizeof(double), ctx->st));
+    DQ_CK(cudaMemsetAsync(g.gacc, 0, g.C * 3 * sizeof(double), g.st));
     int maxlen = 0;
     for (int j = 0; j < g.nc; ++j) maxlen = std::max(maxlen, g.cp[j + 1] - g.cp[j]);
     KronArgs wl = kron_base(g, kB, kron_nv(g, true));
@@ -783,28 +883,28 @@ int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda, double* lo
     for (int step = 0; step < maxlen; ++step) {
       DQ_CLASS(ctx, kTGrad);
       DQ_LAUNCH(ctx, launch_grad_terms(g.A1, g.nn(), g.nc + 1, g.d_cp_grad, step, g.p.Lx, g.p.Ly,
-                                       g.L, g.field, g.p.dtau, g.gacc, batch, ctx->st));
+                                       g.L, g.field, g.p.dtau, g.gacc, batch, g.st));
       if (step + 1 < maxlen) {
         wl.step = wr.step = step;
         DQ_CLASS(ctx, kTGrad);
-        DQ_LAUNCH(ctx, launch_kron_cols<double>(g.A1, batch, wl, ctx->st));
+        DQ_LAUNCH(ctx, launch_kron_cols<double>(g.A1, batch, wl, g.st));
         DQ_CLASS(ctx, kTGrad);
-        DQ_LAUNCH(ctx, launch_kron_rows<double>(g.A1, g.A1, batch, wr, ctx->st));
+        DQ_LAUNCH(ctx, launch_kron_rows<double>(g.A1, g.A1, batch, wr, g.st));
       }
     }
     // results into W2 scratch: [0, C) dt, [C, 2C) dlambda, [2C, 3C) logW
     double* tmp = g.W2;
     DQ_CLASS(ctx, kTMisc);
-    DQ_LAUNCH(ctx, (k_pick3<<<1, 256, 0, ctx->st>>>(g.gacc, tmp, tmp + g.C, g.C), cudaGetLastError()));
+    DQ_LAUNCH(ctx, (k_pick3<<<1, 256, 0, g.st>>>(g.gacc, tmp, tmp + g.C, g.C), cudaGetLastError()));
     DQ_CLASS(ctx, kTMisc);
-    DQ_LAUNCH(ctx, (k_logw<<<g.C, 256, 0, ctx->st>>>(g.LD, static_cast<long long>(g.nc + 1) * g.N,
+    DQ_LAUNCH(ctx, (k_logw<<<g.C, 256, 0, g.st>>>(g.LD, static_cast<long long>(g.nc + 1) * g.N,
                                                       g.logabs, g.nc + 1, g.field, g.L, g.N, g.lam,
                                                       tmp + 2 * g.C),
                     cudaGetLastError()));
     const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    if (dlogW_dt) DQ_CK(cudaMemcpyAsync(dlogW_dt + off, tmp, g.C * 8, kind, ctx->st));
-    if (dlogW_dlambda) DQ_CK(cudaMemcpyAsync(dlogW_dlambda + off, tmp + g.C, g.C * 8, kind, ctx->st));
-    if (logW) DQ_CK(cudaMemcpyAsync(logW + off, tmp + 2 * g.C, g.C * 8, kind, ctx->st));
+    if (dlogW_dt) DQ_CK(cudaMemcpyAsync(dlogW_dt + off, tmp, g.C * 8, kind, g.st));
+    if (dlogW_dlambda) DQ_CK(cudaMemcpyAsync(dlogW_dlambda + off, tmp + g.C, g.C * 8, kind, g.st));
+    if (logW) DQ_CK(cudaMemcpyAsync(logW + off, tmp + 2 * g.C, g.C * 8, kind, g.st));
     off += g.C;
   }
   if (!out_on_device) return check_status(ctx);
@@ -918,6 +1018,7 @@ int64_t dqmc_launch_count(const dqmc_ctx* ctx) { return ctx ? ctx->launches : DQ
 
 int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode) {
   if (!ctx || (mode != DQMC_GEMM_TENSOR && mode != DQMC_GEMM_FP64)) return DQMC_ERR_ARG;
+  if (ctx->gemm_mode != mode) drop_graphs(ctx);
   ctx->gemm_mode = mode;
   return DQMC_OK;
 }

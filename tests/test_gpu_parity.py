@@ -105,6 +105,43 @@ def test_two_groups_in_one_context_match_oracle():
                 chain += 1
 
 
+def test_graph_replay_equals_direct_launches():
+    """Captured sweep graphs (groups on concurrent branches) give bit-identical
+    fields and G to one-by-one launches in group order."""
+    groups = [_grp(4, 4, beta=1.0, ns=3, k=4, C=2), _grp(8, 6, U=3.0, beta=1.5, dtau=0.25, ns=2, k=8, C=3, prec="df32")]
+    with _sim(groups, seed=8) as a, _sim(groups, seed=8) as b:
+        b.use_graphs(False)
+        a.sweep(3, measure=True)
+        b.sweep(3, measure=True)
+        for fa, fb in zip(a.field(), b.field()):
+            assert np.array_equal(fa, fb)
+        for c in range(5):
+            assert np.array_equal(a.G(c, 0), b.G(c, 0))
+        np.testing.assert_array_equal(a.observables(), b.observables())
+
+
+def test_uneven_batch_of_six_lattices_matches_oracle():
+    """Six cluster sizes (N = 4 .. 100) with different U, beta, dtau, n_s, k and
+    precisions in one context; one sweep of every chain against the oracle."""
+    groups = [_grp(2, 2, U=1.0, beta=1.0, dtau=0.25, ns=2, k=2, C=2),
+              _grp(4, 2, U=2.0, beta=1.0, dtau=0.2, ns=3, k=4, C=1, prec="df32"),
+              _grp(6, 6, U=3.0, beta=0.5, dtau=0.1, ns=2, k=8, C=1),
+              _grp(8, 8, U=2.0, beta=0.5, dtau=0.125, ns=4, k=16, C=1, prec="df32"),
+              _grp(10, 6, U=1.0, beta=0.6, dtau=0.2, ns=3, k=8, C=1),
+              _grp(10, 10, U=2.0, beta=0.25, dtau=0.125, ns=2, k=32, C=1, prec="df32")]
+    with _sim(groups, seed=17) as sim:
+        sim.sweep(1)
+        fields = sim.field()
+        chain = 0
+        for gi, g in enumerate(groups):
+            for c in range(g.n_chains):
+                ch = o.Chain(_params(g), seed=17, chain=chain)
+                out = ch.sweep()
+                assert np.array_equal(fields[gi][c], ch.field), (gi, c)
+                assert _rel(sim.G(chain, 0), out["G_up"]) < GTOL
+                chain += 1
+
+
 # -- replayed fields, stabilisation at low temperature -----------------------
 def test_set_field_low_temperature_green():
     g = _grp(8, 8, U=2.0, beta=20.0, dtau=0.2, ns=8, C=2)
