@@ -378,6 +378,12 @@ def run_config(args):
     precs = ("fp64",) if args.config == "c5" else ("df32", "fp64", "fp32")
     for prec in precs:
         groups = config_groups(pkg, args.config, prec)
+        tuned = None
+        if args.autotune > 0 and args.config in ("c2", "c4"):
+            t0 = time.perf_counter()
+            groups = pkg.autotune(groups, drift_target=args.autotune)
+            tuned = {"target": args.autotune, "seconds": time.perf_counter() - t0,
+                     "n_s": [g.stab_interval for g in groups], "k": [g.delay_k for g in groups]}
         with pkg.DQMC(groups, seed=0) as sim:
             n_up = sum(g.n_chains * g.N * g.L for g in groups)
             gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
@@ -404,7 +410,7 @@ def run_config(args):
             d, a = sim.stats()
             print(json.dumps({"config": args.config, "precision": prec, "ms_per_step": ms,
                               "updates_per_s": n_up / (ms / 1e3), "chains": sim.n_chains,
-                              "drift_max": float(d.max()),
+                              "drift_max": float(d.max()), "autotune": tuned,
                               "acceptance": float(a.sum()) / (n_up * args.steps)}), flush=True)
 
 
@@ -447,6 +453,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--config", default="", choices=["", "c1", "c2", "c4", "c5"],
                     help="time a secondary configuration instead of the headline workload")
+    ap.add_argument("--autotune", type=float, default=0.0,
+                    help="with --config c2/c4: tune n_s and k for this drift target first")
     ap.add_argument("--profile-case", action="store_true",
                     help="run the small ncu capture case (16x16, L=20) and exit")
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])

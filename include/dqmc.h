@@ -106,6 +106,18 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed,
  * synchronising call.  Errors: DQMC_ERR_ARG, DQMC_ERR_CUDA. */
 int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure);
 
+/* Autotuner: for each group choose the stabilisation interval and the delay
+ * depth for this GPU.  n_s: all candidates (L, 64, 48, ..., 3, 2 that are
+ * <= L) run side by side in one probe context of 4 chains each; after two
+ * warm-up sweeps the largest n_s whose G drift over three sweeps stays below
+ * drift_target / 20 is taken (1 if none; the drift over many chains and
+ * sweeps is heavy-tailed, hence the margin).  k: the fastest of 8, 16, 32 at that
+ * n_s (8 chains, two timed sweeps).  out receives copies of groups with
+ * stab_interval and delay_k replaced.  Creates and destroys its own contexts
+ * on `stream`.  Errors: as dqmc_init. */
+int dqmc_autotune(const dqmc_group* groups, int n_groups, double drift_target, uint64_t seed,
+                  void* stream, dqmc_group* out);
+
 /* Sweeps are replayed as one CUDA graph per measure flag (captured at the
  * first dqmc_sweep: one branch per group, the groups run concurrently); with
  * on = 0, or while timing is enabled, kernels are launched one by one on the

@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Group", "DQMC", "LogWeight", "DqmcError", "n_slices"]
+__all__ = ["Group", "DQMC", "LogWeight", "DqmcError", "n_slices", "autotune"]
 
 DqmcError = _lib.DqmcError
 _LIB = None
@@ -217,6 +217,24 @@ class DQMC:
             out.append(flat[off:off + n].reshape(shp))
             off += n
         return out
+
+
+def autotune(groups, drift_target=1e-6, seed=0):
+    """Groups with stab_interval and delay_k chosen by the library's autotuner
+    for this GPU (see dqmc_autotune)."""
+    import torch
+    groups = list(groups)
+    arr = (_lib.DqmcGroup * len(groups))(*[g._c() for g in groups])
+    out = (_lib.DqmcGroup * len(groups))()
+    st = torch.cuda.current_stream().cuda_stream
+    _lib.check(lib().dqmc_autotune(arr, len(groups), float(drift_target), int(seed),
+                                   ctypes.c_void_p(st), out), "dqmc_autotune", lib())
+    res = []
+    for g, o in zip(groups, out):
+        res.append(Group(Lx=g.Lx, Ly=g.Ly, t=g.t, U=g.U, beta=g.beta, dtau=g.dtau,
+                         n_chains=g.n_chains, stab_interval=int(o.stab_interval),
+                         delay_k=int(o.delay_k), precision=g.precision))
+    return res
 
 
 class LogWeight:

@@ -134,6 +134,7 @@ struct dqmc_ctx {
 namespace {
 
 constexpr int kOzakiMinN = 64;  // smaller matrices stay on the FP64 pipe
+constexpr double kTuneMargin = 0.05;  // probe drift must stay below 5% of the target
 
 thread_local cudaError_t g_last_cuda = cudaSuccess;  // last failing CUDA call (this thread)
 thread_local int g_last_line = 0;
@@ -759,6 +760,83 @@ int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure) {
   for (int s = 0; s < n_sweeps; ++s) {
     DQ_CK(cudaGraphLaunch(ctx->gexec[m], ctx->st));
     ctx->launches += ctx->graph_launches[m];
+  }
+  return DQMC_OK;
+}
+
+int dqmc_autotune(const dqmc_group* groups, int n_groups, double drift_target, uint64_t seed,
+                  void* stream, dqmc_group* out) {
+  if (!groups || n_groups < 1 || !out || !(drift_target > 0.0)) return DQMC_ERR_ARG;
+  for (int i = 0; i < n_groups; ++i) DQ_RET(validate(groups[i]));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int gi = 0; gi < n_groups; ++gi) {
+    const dqmc_group& g = groups[gi];
+    const int L = static_cast<int>(std::llround(g.beta / g.dtau));
+    // Candidate stabilisation intervals, largest first; all probed at once.
+    std::vector<int> cands;
+    for (int ns : {L, 64, 48, 40, 32, 25, 20, 16, 12, 10, 8, 6, 5, 4, 3, 2})
+      if (ns <= L && ns >= 2 && (cands.empty() || ns < cands.back())) cands.push_back(ns);
+    std::vector<dqmc_group> probe;
+    for (int ns : cands) {
+      dqmc_group p = g;
+      p.n_chains = std::min(g.n_chains, 4);
+      p.stab_interval = ns;
+      probe.push_back(p);
+    }
+    dqmc_ctx* pc = nullptr;
+    DQ_RET(dqmc_init(probe.data(), static_cast<int>(probe.size()), seed, stream, &pc));
+    int rc = dqmc_sweep(pc, 2, 0);
+    if (rc == DQMC_OK) rc = dqmc_reset_stats(pc);
+    if (rc == DQMC_OK) rc = dqmc_sweep(pc, 3, 0);
+    std::vector<double> drift(pc->total);
+    if (rc == DQMC_OK) rc = dqmc_get_stats(pc, drift.data(), nullptr);
+    dqmc_destroy(pc);
+    DQ_RET(rc);
+    int chosen = 1;
+    for (size_t c = 0; c < cands.size(); ++c) {
+      const int per = probe[c].n_chains;
+      double dmax = 0.0;
+      for (int q = 0; q < per; ++q) dmax = std::max(dmax, drift[c * per + q]);
+      // The drift over chains and sweeps is heavy-tailed: a probe of a few
+      // chains must sit well below the target to keep a long run under it.
+      if (dmax <= kTuneMargin * drift_target) {
+        chosen = cands[c];
+        break;
+      }
+    }
+    // Delay depth: fastest of 8, 16, 32 at the chosen interval.
+    dqmc_group best = g;
+    best.stab_interval = chosen;
+    float best_ms = 0.0f;
+    for (int k : {8, 16, 32}) {
+      dqmc_group p = best;
+      p.delay_k = k;
+      p.n_chains = std::min(g.n_chains, 8);
+      dqmc_ctx* kc = nullptr;
+      DQ_RET(dqmc_init(&p, 1, seed, stream, &kc));
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      float ms = 0.0f;
+      int r = dqmc_sweep(kc, 1, 0);
+      if (r == DQMC_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        r = DQMC_ERR_CUDA;
+      if (r == DQMC_OK) {
+        cudaEventRecord(e0, st);
+        r = dqmc_sweep(kc, 2, 0);
+        cudaEventRecord(e1, st);
+        if (r == DQMC_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+          r = DQMC_ERR_CUDA;
+      }
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+      dqmc_destroy(kc);
+      DQ_RET(r);
+      if (best_ms == 0.0f || ms < best_ms) {
+        best_ms = ms;
+        best.delay_k = k;
+      }
+    }
+    out[gi] = best;
   }
   return DQMC_OK;
 }

@@ -142,6 +142,21 @@ def test_uneven_batch_of_six_lattices_matches_oracle():
                 chain += 1
 
 
+def test_autotuner_respects_the_drift_target():
+    import paper_1504_05090_gb300 as pkg
+    g = _grp(4, 4, U=2.0, beta=10.0, dtau=0.125, ns=10, k=8, C=4)
+    tight = pkg.autotune([g], drift_target=1e-11)[0]
+    loose = pkg.autotune([g], drift_target=1e-5)[0]
+    assert 1 <= tight.stab_interval <= loose.stab_interval <= g.L
+    assert tight.delay_k in (8, 16, 32)
+    with _sim([tight], seed=6) as sim:
+        sim.sweep(2)
+        sim.reset_stats()
+        sim.sweep(3)
+        drift, _ = sim.stats()
+        assert np.all(drift < 4e-11), (tight.stab_interval, drift)
+
+
 # -- replayed fields, stabilisation at low temperature -----------------------
 def test_set_field_low_temperature_green():
     g = _grp(8, 8, U=2.0, beta=20.0, dtau=0.2, ns=8, C=2)
