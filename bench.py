@@ -180,42 +180,76 @@ def kernel_profile(sim, gbuf, steps, torch):
     return t
 
 
-def algorithmic_flops_per_sweep(cls, chains):
-    """FP64 flops per sweep of the FP64 linear-algebra classes (what the method
-    must compute, counted from the formulas, not from the kernels)."""
-    N, L, ns = n_sites(), n_slices(), W["ns"]
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+# Peaks.  FP64 pipe: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz (unit counts and
+# the maximum SM clock).  FP32 pipe: 152 x 128 FMA/clk x 2 x 2070 MHz; a float-pair
+# (df32) multiply-add of the sweep kernels costs 14 FP32 instructions (TwoProd,
+# TwoSum, operand loads), so the df32 arithmetic ceiling is 2 x 152 x 128 x 2.07e9 / 14.
+FP64_PEAK = 152 * 2 * 2 * 2.07e9 / 1e12
+DF32_PEAK = 2 * 152 * 128 * 2.07e9 / 14 / 1e12
+
+
+def class_work(cls, acceptance, precision):
+    """Algorithmic work of one sweep of the benchmark workload for a kernel
+    class: (units, amount, bound).  Counted from the formulas of the method,
+    not from what the kernels execute."""
+    N, L, ns, C = n_sites(), n_slices(), W["ns"], W["chains"]
+    Lx, Ly = W["Lx"], W["Ly"]
     nc = -(-L // ns)
-    g = 2.0 * N ** 3
+    g3 = 2.0 * N ** 3
     if cls == "gemm_f64":
-        # T updates (2 nc), recompute Mid + G (4 per point, nc points), G(tau) (6 per point, nc+1)
-        return chains * g * (2 * nc + 4 * nc + 6 * (nc + 1))
-    if cls == "qr_pivot":
-        # Householder R (4/3 N^3) + explicit Q (4/3 N^3), both stacks
-        return chains * 2 * nc * (8.0 / 3.0) * N ** 3
-    if cls == "gj_inverse":
-        return chains * (nc + (nc + 1)) * g
-    return None
+        # T updates (2 nc), recompute Mid + W1 + G (4 per point, nc points),
+        # G(tau) Mid + W1 + G(l,0) + W2 + Y (6 per point, nc + 1); on the tensor
+        # cores each FP64 product is 36 BF16 digit products.
+        fp64eq = C * g3 * (2 * nc + 4 * nc + 6 * (nc + 1))
+        return "tensor", 36 * fp64eq
+    if cls == "qr_pivot":  # Householder R and explicit Q, both stacks
+        return "alu64", C * 2 * nc * (8.0 / 3.0) * N ** 3
+    if cls == "gj_inverse":  # nc recomputes + (nc + 1) stabilisation points for G(tau)
+        return "alu64", C * (2 * nc + 1) * g3
+    if cls in ("stack_kron", "gtau_propagate"):
+        # two matrices (right and left stack; G(l,0) and Y) x L slices x N vectors
+        # x 2N(Lx+Ly) flops per Kronecker application
+        return "alu64", C * 2 * L * N * 2 * N * (Lx + Ly)
+    if cls == "metropolis":  # rank-1 Sherman-Morrison update per accepted flip
+        return ("alu32x2" if precision == "df32" else "alu"), acceptance * C * N * L * 2.0 * N * N
+    if cls == "wrap":  # B G B^-1 by Kronecker factors: 2 sides x N vectors x 2N(Lx+Ly)
+        return ("alu32x2" if precision == "df32" else "alu"), C * L * 2 * N * 2 * N * (Lx + Ly)
+    return None, None
 
 
-def roofline(profile, steps, peaks):
-    cls, (ms, n) = max(profile.items(), key=lambda kv: kv[1][0])
-    fl = algorithmic_flops_per_sweep(cls, W["chains"])
-    if fl is None or n == 0:
-        return {"bound": "latency", "kernel": cls, "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None}
-    per_launch = fl * steps / n
-    avg_s = ms / n / 1e3
-    ach = per_launch / avg_s / 1e12
-    peak = peaks["fp64_tflops"]
-    return {"bound": "alu", "kernel": cls, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-            "frac": ach / peak, "traffic": None, "peak_source": peaks["fp64_source"],
-            "flops_per_launch": per_launch, "avg_launch_ms": ms / n, "launches": n}
-
-
-def fp64_peak():
-    # FP64 issue rate from unit counts and clock: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz.
-    return {"fp64_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
-            "fp64_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz max SM clock"}
+def roofline(profile, steps, acceptance, precision="df32"):
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained")
+    rows = {}
+    for cls, (ms, n) in profile.items():
+        bound, work = class_work(cls, acceptance, precision)
+        if bound is None or n == 0 or ms <= 0:
+            continue
+        ach = work * steps / (ms / 1e3) / 1e12
+        if bound == "tensor":
+            peak, src = (bf16, "measured bf16 GEMM, sustained (MEASURED_PEAKS.json)") if bf16 else \
+                (1700.0, "fallback 1.7 PFLOP/s bf16 sustained")
+        elif bound == "alu64":
+            peak, src = FP64_PEAK, "derived FP64 pipe: 152 SMs x 2 FMA/clk x 2 x 2070 MHz"
+        elif bound == "alu32x2":
+            peak, src = DF32_PEAK, "derived df32: FP32 pipe 152 x 128 FMA/clk x 2 x 2070 MHz / 14 instr"
+        else:
+            peak, src = 2 * 152 * 128 * 2.07e9 / 1e12, "derived FP32 pipe: 152 x 128 FMA/clk x 2 x 2070 MHz"
+        rows[cls] = {"bound": "tensor" if bound == "tensor" else "alu", "kernel": cls,
+                     "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                     "traffic": None, "peak_source": src,
+                     "flops_per_launch": work * steps / n, "avg_launch_ms": ms / n, "launches": n}
+    dom = max(profile.items(), key=lambda kv: kv[1][0])[0]
+    return rows.get(dom, {"bound": "alu", "kernel": dom, "achieved": None, "peak": None,
+                          "unit": "TFLOP/s", "frac": None, "traffic": None}), rows
 
 
 def e2e_arm(pkg, torch, sim, steps):
@@ -275,6 +309,7 @@ def run_ours(args):
         return float(t.item())
 
     ms = slowest(mixed["ms"])
+    roof, roof_rows = roofline(prof, args.steps, mixed["acceptance"], "df32")
     ms64 = slowest(plain["ms"])
     value = world * updates_per_sweep(W["chains"]) / (ms / 1e3)
     if rank == 0:
@@ -294,7 +329,8 @@ def run_ours(args):
                              (slowest(arms["fp32"]["ms"]) / 1e3),
                              "ms_per_step": arms["fp32"]["ms"], "drift": arms["fp32"]["drift"],
                              "kernel_ms_per_step": arms["fp32"]["kernel_ms_per_step"]},
-            "roofline": roofline(prof, args.steps, fp64_peak()),
+            "roofline": roof,
+            "roofline_by_class": roof_rows,
             "kernel_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "e2e": e2e, "gpu_launches": mixed["launches"], "clocks": mixed["clocks"],
         }

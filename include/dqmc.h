@@ -195,6 +195,15 @@ int64_t dqmc_launch_count(const dqmc_ctx* ctx);
 #define DQMC_GEMM_FP64 1
 int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode);
 
+/* CTAs per chain in the Metropolis pass (the site loop of Sec. 2 with the
+ * delayed updates of G, Eq. (3)): 1, 2 or 4 CTAs of one thread-block cluster
+ * share a chain, each folding the pending rank-k update into its own block of
+ * rows of G; 0 (default) picks the largest of 4, 2, 1 for which all chains'
+ * CTAs fit on the SMs at once.  The result does not depend on the split: the
+ * CTAs take identical decisions and every element of G is formed by the same
+ * operations.  Errors: DQMC_ERR_ARG for another value. */
+int dqmc_set_metropolis_split(dqmc_ctx* ctx, int ctas_per_chain);
+
 /* Optional per-launch timing (library tracing).  While enabled, every kernel
  * launch is bracketed by a pair of CUDA events on the context's stream and its
  * device time is added to the class of the kernel (metropolis, wrap,

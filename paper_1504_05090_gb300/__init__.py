@@ -160,6 +160,11 @@ class DQMC:
         code = {"tensor": _lib.DQMC_GEMM_TENSOR, "fp64": _lib.DQMC_GEMM_FP64}[mode]
         _lib.check(lib().dqmc_set_gemm_mode(self._h, code), "dqmc_set_gemm_mode", lib())
 
+    def set_metropolis_split(self, ctas_per_chain=0):
+        """CTAs per chain in the Metropolis pass: 1, 2, 4, or 0 for automatic."""
+        _lib.check(lib().dqmc_set_metropolis_split(self._h, int(ctas_per_chain)),
+                   "dqmc_set_metropolis_split", lib())
+
     def timing(self, on=True):
         """Enable/disable per-launch CUDA-event timing by kernel class."""
         _lib.check(lib().dqmc_timing_enable(self._h, int(bool(on))), "dqmc_timing_enable", lib())

@@ -54,6 +54,7 @@ SIGNATURES = {
     "dqmc_num_chains": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "dqmc_set_gemm_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "dqmc_set_metropolis_split": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_use_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_autotune": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_int, ctypes.c_double,
                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(DqmcGroup)]),

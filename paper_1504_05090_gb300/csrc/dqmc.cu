@@ -127,6 +127,8 @@ struct dqmc_ctx {
   uint32_t* d_sweep = nullptr;
   int* d_status = nullptr;
   int total = 0;
+  int nsm = 0;       // SMs of the device
+  int metro_cs = 0;  // CTAs per chain in the Metropolis pass (0 = automatic)
   long long launches = 0;
   std::vector<void*> allocs;
 };
@@ -451,6 +453,16 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
   ma.ep2h = static_cast<float>(ep2);
   ma.ep2l = static_cast<float>(ep2 - static_cast<double>(ma.ep2h));
   ma.accepted = g.acc;
+  ma.status = ctx->d_status;
+  ma.cs = ctx->metro_cs;
+  if (ma.cs == 0) {  // all chains of all groups run their Metropolis passes side by side
+    ma.cs = 1;
+    for (int cs : {4, 2})
+      if (static_cast<long long>(cs) * ctx->total <= ctx->nsm && g.N >= 4 * cs) {
+        ma.cs = cs;
+        break;
+      }
+  }
   const bool fp64 = sizeof(T) == 8;
   KronArgs wl = kron_base(g, kB, kron_nv(g, fp64));
   KronArgs wr = kron_base(g, kBIT, kron_nv(g, fp64));
@@ -696,6 +708,7 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
   if (!ctx) return DQMC_ERR_OOM;
   ctx->st = static_cast<cudaStream_t>(stream);
   ctx->seed = seed;
+  ctx->nsm = prop.multiProcessorCount;
   ctx->g.resize(n_groups);
   int rc = dev_alloc(ctx, &ctx->d_sweep, sizeof(uint32_t));
   if (rc == DQMC_OK) rc = dev_alloc(ctx, &ctx->d_status, sizeof(int));
@@ -1098,6 +1111,15 @@ int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode) {
   if (!ctx || (mode != DQMC_GEMM_TENSOR && mode != DQMC_GEMM_FP64)) return DQMC_ERR_ARG;
   if (ctx->gemm_mode != mode) drop_graphs(ctx);
   ctx->gemm_mode = mode;
+  return DQMC_OK;
+}
+
+int dqmc_set_metropolis_split(dqmc_ctx* ctx, int ctas_per_chain) {
+  if (!ctx || (ctas_per_chain != 0 && ctas_per_chain != 1 && ctas_per_chain != 2 &&
+               ctas_per_chain != 4))
+    return DQMC_ERR_ARG;
+  if (ctx->metro_cs != ctas_per_chain) drop_graphs(ctx);
+  ctx->metro_cs = ctas_per_chain;
   return DQMC_OK;
 }
 

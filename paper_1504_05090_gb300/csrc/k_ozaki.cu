@@ -16,10 +16,14 @@
 // Digits beyond p + q = 7 are below 2^-56 relative and dropped.
 //
 // Tile: one CTA computes 128 x 64 of C for one matrix, K streamed in chunks of
-// 64; all 8 digit slices of the chunk sit in shared memory (128 + 64 KB) in the
-// no-swizzle K-major core-matrix layout (8 rows x 16 bytes per core matrix).
-// One thread issues the 36 x 4 MMAs of a chunk (M = 128, N = 64, K = 16) and
-// commits them to an mbarrier; the CTA owns all 512 TMEM columns (8 x 64).
+// 32.  The split kernel writes the digit slices tile-blocked, each (slice, row
+// tile, K chunk) block contiguous in the no-swizzle K-major core-matrix order
+// (8 rows x 16 bytes per core matrix), so one thread moves a chunk -- all 8
+// slices of A and B, 96 KB -- with 16 bulk async copies (cp.async.bulk)
+// completing on an mbarrier.  Two stages: the copy of chunk c + 1 runs while
+// the tensor pipe works on the 36 x 2 MMAs (M = 128, N = 64, K = 16) of chunk
+// c; MMA completion is committed to a second mbarrier per stage.  The CTA owns
+// all 512 TMEM columns (8 accumulators x 64).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -29,11 +33,25 @@ namespace dqmc {
 namespace {
 
 constexpr int kS = 8;
-constexpr int kTM = 128, kTN = 64, kTK = 64;
-constexpr int kATile = kTM * kTK * 2;
-constexpr int kBTile = kTN * kTK * 2;
-constexpr int kOzSmem = kS * (kATile + kBTile);
+constexpr int kTM = 128, kTN = 64, kTK = 32;
+constexpr int kATile = kTM * kTK * 2;  // bytes of one digit slice of an A chunk (8 KB)
+constexpr int kBTile = kTN * kTK * 2;  // (4 KB)
+constexpr int kStage = kS * (kATile + kBTile);  // 96 KB: all digits of one K chunk
+constexpr int kStages = 2;
+constexpr int kOzSmem = kStages * kStage;
 constexpr long long kWaitLimit = 1LL << 26;
+
+// Element offset of (slice p, vector v, k) in the tile-blocked digit layout:
+// blocks [p][row tile][K chunk] of R x kTK elements, each block in the
+// no-swizzle K-major core-matrix order (8 rows x 8 elements per core matrix,
+// core matrices along K first), so that one K chunk of one slice of one row
+// tile is a single contiguous run for a bulk copy.
+__host__ __device__ __forceinline__ size_t oz_offset(int p, int v, int k, int R, int nrt, int nkc) {
+  const int rt = v / R, r = v - rt * R, kc = k / kTK, kk = k - kc * kTK;
+  const size_t block = (static_cast<size_t>(p) * nrt + rt) * nkc + kc;
+  return block * (static_cast<size_t>(R) * kTK) + (r >> 3) * (kTK / 8 * 64) + (kk >> 3) * 64 +
+         (r & 7) * 8 + (kk & 7);
+}
 
 __device__ __forceinline__ double oz_scale(const double* p, int mode, int i) {
   if (mode == 0 || p == nullptr) return 1.0;
@@ -47,12 +65,14 @@ __device__ __forceinline__ double oz_scale(const double* p, int mode, int i) {
 }
 
 // One warp per vector v of the batch entry: element k of vector v is
-// M[v sv + k sk] (times the inner scale of k).  Writes the 8 digit slices
-// out[p][v][k] (row length np, zero tail) and the scale exponent ex[v].
-__global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long sM, int n, int np,
+// M[v sv + k sk] (times the inner scale of k).  Writes the 8 digit slices in
+// the tile-blocked layout (rows padded to a multiple of R, K to a multiple of
+// the chunk, zero padding) and the scale exponent ex[v].
+__global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long sM, int n, int R,
                                                  long long sv, long long sk, const double* ksall,
                                                  long long sks, int ks_mode, __nv_bfloat16* outall,
                                                  long long sOut, int* exall, long long sEx) {
+  const int nrt = (n + R - 1) / R, nkc = (n + kTK - 1) / kTK, np = nkc * kTK;
   const int b = blockIdx.y;
   const double* M = Mall + b * sM;
   __shared__ double ksv[kMaxN];
@@ -60,8 +80,13 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
   for (int k = threadIdx.x; k < n; k += blockDim.x) ksv[k] = oz_scale(ks, ks_mode, k);
   __syncthreads();
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (v >= n) return;
+  if (v >= nrt * R) return;
   __nv_bfloat16* out = outall + b * sOut;
+  if (v >= n) {  // padding rows of the last row tile
+    for (int k = lane; k < np; k += 32)
+      for (int p = 0; p < kS; ++p) out[oz_offset(p, v, k, R, nrt, nkc)] = __float2bfloat16_rn(0.0f);
+    return;
+  }
   int emax = -2000;
   for (int k = lane; k < n; k += 32) {
     const double x = (ks_mode != 0) ? M[v * sv + k * sk] * ksv[k] : M[v * sv + k * sk];
@@ -89,7 +114,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
     for (int p = 0; p < kS; ++p) {
       const int a = (p < 7) ? static_cast<int>((al >> (46 - 7 * p)) & 127ULL)
                             : static_cast<int>((al & 15ULL) << 3);
-      out[(static_cast<size_t>(p) * n + v) * np + k] = __float2bfloat16_rn(sg * static_cast<float>(a));
+      out[oz_offset(p, v, k, R, nrt, nkc)] = __float2bfloat16_rn(sg * static_cast<float>(a));
     }
   }
 }
@@ -101,27 +126,47 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // Shared-memory matrix descriptor: no swizzle, K-major; LBO = distance of the
 // next core matrix along K, SBO = along M/N (bytes, encoded >> 4), version 1.
 __device__ __forceinline__ uint64_t oz_desc(uint32_t addr) {
-  constexpr uint32_t lbo = 128, sbo = (kTK / 8) * 128;
+  constexpr uint32_t lbo = 128, sbo = (kTK / 8) * 128;  // 128 B, 512 B
   return static_cast<uint64_t>((addr >> 4) & 0x3FFF) |
          (static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16) |
          (static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32) | (1ULL << 46);
 }
 
-// Digit slices [kS][n][np] of rows r0 .. r0+R-1 and k0 .. k0+kTK-1 into shared
-// memory, core-matrix layout; rows >= n and k >= np are zero.
-__device__ __forceinline__ void oz_load(unsigned char* sm, const __nv_bfloat16* src, int n, int np,
-                                        int r0, int R, int k0) {
-  const int chunks = kS * R * (kTK / 8);
-  for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
-    const int kg = c % (kTK / 8);
-    const int r = (c / (kTK / 8)) % R;
-    const int p = c / ((kTK / 8) * R);
-    const int gr = r0 + r, gk = k0 + kg * 8;
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (gr < n && gk < np)
-      v = *reinterpret_cast<const uint4*>(src + (static_cast<size_t>(p) * n + gr) * np + gk);
-    const int off = p * (R * kTK * 2) + (r >> 3) * ((kTK / 8) * 128) + kg * 128 + (r & 7) * 16;
-    *reinterpret_cast<uint4*>(sm + off) = v;
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait on an mbarrier phase; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, int parity) {
+  uint32_t done = 0;
+  for (long long it = 0; it < kWaitLimit && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity));
+  return done != 0;
+}
+
+// One thread: bulk-copy all digit slices of K chunk kc (A rows of tile ra, B
+// rows of tile rb) into stage smem; completion is counted on `bar`.
+__device__ __forceinline__ void oz_issue_chunk(unsigned char* stage, const __nv_bfloat16* As,
+                                               const __nv_bfloat16* Bs, int ra, int rb, int kc,
+                                               int nrtA, int nrtB, int nkc, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(static_cast<uint32_t>(kStage)));
+  for (int p = 0; p < kS; ++p) {
+    const __nv_bfloat16* ga = As + ((static_cast<size_t>(p) * nrtA + ra) * nkc + kc) * (kTM * kTK);
+    const __nv_bfloat16* gb = Bs + ((static_cast<size_t>(p) * nrtB + rb) * nkc + kc) * (kTN * kTK);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(stage + p * kATile)),
+        "l"(ga), "r"(static_cast<uint32_t>(kATile)), "r"(smem_u32(bar))
+        : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(stage + kS * kATile + p * kBTile)),
+        "l"(gb), "r"(static_cast<uint32_t>(kBTile)), "r"(smem_u32(bar))
+        : "memory");
   }
 }
 
@@ -136,7 +181,7 @@ struct OzMmaArgs {
   long long sExB;
   double* C;
   long long sC;
-  int n, np;
+  int n;
   const double* rs;
   long long srs;
   int rs_mode;
@@ -149,14 +194,14 @@ struct OzMmaArgs {
 
 __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   extern __shared__ __align__(1024) unsigned char oz_sm[];
-  unsigned char* smA = oz_sm;
-  unsigned char* smB = oz_sm + kS * kATile;
-  __shared__ uint64_t bar;
+  __shared__ uint64_t full[kStages], mmad[kStages];
   __shared__ uint32_t tmem_sh;
+  __shared__ int fail_sh;
   const int b = blockIdx.z;
   const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * kTN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = a.n, np = a.np;
+  const int n = a.n;
+  const int nrtA = (n + kTM - 1) / kTM, nrtB = (n + kTN - 1) / kTN, nkc = (n + kTK - 1) / kTK;
   const __nv_bfloat16* As = a.As + b * a.sAs;
   const __nv_bfloat16* Bs = a.Bs + b * a.sBs;
   if (warp == 0) {
@@ -164,7 +209,11 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    for (int s2 = 0; s2 < kStages; ++s2) {
+      mbar_init(&full[s2], 1);
+      mbar_init(&mmad[s2], 1);
+    }
+    fail_sh = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -173,22 +222,32 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   const uint32_t tbase = tmem_sh;
   // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N, M.
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
-  int phase = 0;
-  bool ok = true;
-  for (int k0 = 0; k0 < np; k0 += kTK) {
-    oz_load(smA, As, n, np, i0, kTM, k0);
-    oz_load(smB, Bs, n, np, j0, kTN, k0);
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    // Producer and MMA issuer.  Chunk c sits in stage c & 1.  After the MMAs
+    // of chunk c are queued, the MMAs of chunk c - 1 (queued earlier, so done
+    // first) are awaited and chunk c + 1 is loaded into their stage while the
+    // tensor pipe works on chunk c.
+    int pend_load[kStages] = {-1, -1};  // parity of an outstanding load per stage
+    int committed = -1;                 // last chunk whose MMAs were committed
+    oz_issue_chunk(oz_sm, As, Bs, blockIdx.y, blockIdx.x, 0, nrtA, nrtB, nkc, &full[0]);
+    pend_load[0] = 0;
+    for (int c = 0; c < nkc; ++c) {
+      const int st = c & 1;
+      if (!mbar_wait(&full[st], (c >> 1) & 1)) {
+        fail_sh = 1;
+        break;
+      }
+      pend_load[st] = -1;
       asm volatile("tcgen05.fence::after_thread_sync;");
+      unsigned char* smA = oz_sm + st * kStage;
+      unsigned char* smB = smA + kS * kATile;
       for (int d = 0; d < kS; ++d)
         for (int p = 0; p <= d; ++p) {
           const int q = d - p;
           for (int ks = 0; ks < kTK / 16; ++ks) {
             const uint64_t ad = oz_desc(smem_u32(smA + p * kATile + ks * 256));
             const uint64_t bd = oz_desc(smem_u32(smB + q * kBTile + ks * 256));
-            const uint32_t acc = (k0 > 0 || p > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred pa;\n setp.ne.u32 pa, %4, 0;\n"
                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tbase + d * kTN),
@@ -196,23 +255,34 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
           }
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(&bar)));
+          smem_u32(&mmad[st])));
+      committed = c;
+      if (c + 1 < nkc) {
+        const int so = st ^ 1;
+        if (c >= 1 && !mbar_wait(&mmad[so], ((c - 1) >> 1) & 1)) {
+          fail_sh = 1;
+          break;
+        }
+        oz_issue_chunk(oz_sm + so * kStage, As, Bs, blockIdx.y, blockIdx.x, c + 1, nrtA, nrtB, nkc,
+                       &full[so]);
+        pend_load[so] = ((c + 1) >> 1) & 1;
+      }
     }
-    uint32_t done = 0;
-    for (long long it = 0; it < kWaitLimit && !done; ++it) {
-      asm volatile(
-          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-          : "=r"(done)
-          : "r"(smem_u32(&bar)), "r"(phase));
+    if (fail_sh) {  // drain what is still in flight before TMEM and smem go away
+      for (int s2 = 0; s2 < kStages; ++s2)
+        if (pend_load[s2] >= 0) mbar_wait(&full[s2], pend_load[s2]);
+      if (committed >= 0) mbar_wait(&mmad[committed & 1], (committed >> 1) & 1);
     }
-    if (!done) {  // bounded wait gave up: record it, leave C untouched, free TMEM
-      ok = false;
-      if (threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
-      break;
-    }
-    phase ^= 1;
-    __syncthreads();
   }
+  __syncthreads();
+  // Everyone waits for the MMAs of the last chunk (tcgen05.commit tracks all
+  // earlier MMAs of the issuing thread, so this covers every chunk).
+  bool ok = fail_sh == 0;
+  if (ok) {
+    const int last = nkc - 1;
+    ok = mbar_wait(&mmad[last & 1], (last >> 1) & 1);
+  }
+  if (!ok && threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     const int i = i0 + warp * 32 + lane;
@@ -260,36 +330,45 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
 
 }  // namespace
 
+static size_t oz_slice_elems(int n, int R) {
+  const size_t nrt = (n + R - 1) / R, nkc = (n + kTK - 1) / kTK;
+  return static_cast<size_t>(kS) * nrt * R * nkc * kTK;
+}
+
 size_t ozaki_scratch_bytes(int n, int max_batch) {
-  const size_t np = (n + 7) / 8 * 8;
-  return static_cast<size_t>(max_batch) * (2ull * kS * n * np * 2 + 2ull * n * sizeof(int)) + 256;
+  return static_cast<size_t>(max_batch) *
+             ((oz_slice_elems(n, kTM) + oz_slice_elems(n, kTN)) * 2 + 2ull * n * sizeof(int)) +
+         1024;
 }
 
 cudaError_t launch_gemm_ozaki(const GemmArgs& g, int batch, void* scratch, int max_batch,
                               int* status, cudaStream_t st) {
   const int n = g.n;
-  const int np = (n + 7) / 8 * 8;
-  const long long sl = static_cast<long long>(kS) * n * np;  // bf16 elements per operand
+  if (n <= 0 || batch <= 0) return cudaSuccess;
+  const long long slA = static_cast<long long>(oz_slice_elems(n, kTM));
+  const long long slB = static_cast<long long>(oz_slice_elems(n, kTN));
   __nv_bfloat16* As = static_cast<__nv_bfloat16*>(scratch);
-  __nv_bfloat16* Bs = As + sl * max_batch;
-  int* exA = reinterpret_cast<int*>(Bs + sl * max_batch);
+  __nv_bfloat16* Bs = As + slA * max_batch;
+  int* exA = reinterpret_cast<int*>(Bs + slB * max_batch);
   int* exB = exA + static_cast<long long>(n) * max_batch;
   cudaError_t e = cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
   if (e != cudaSuccess) return e;
+  const int rowsA = (n + kTM - 1) / kTM * kTM, rowsB = (n + kTN - 1) / kTN * kTN;
   for (int b0 = 0; b0 < batch; b0 += max_batch) {
     const int nb = std::min(max_batch, batch - b0);
     // rows of op(A) diag(ks): tA = 0 -> A[i][k]; tA = 1 -> A[k][i]
-    k_oz_split<<<dim3((n + 7) / 8, nb), 256, 0, st>>>(
-        g.A + b0 * g.sA, g.sA, n, np, g.tA ? 1 : n, g.tA ? n : 1, g.ks ? g.ks + b0 * g.sks : nullptr,
-        g.sks, g.ks ? g.ks_mode : 0, As, sl, exA, n);
+    k_oz_split<<<dim3((rowsA + 7) / 8, nb), 256, 0, st>>>(
+        g.A + b0 * g.sA, g.sA, n, kTM, g.tA ? 1 : n, g.tA ? n : 1,
+        g.ks ? g.ks + b0 * g.sks : nullptr, g.sks, g.ks ? g.ks_mode : 0, As, slA, exA, n);
     // columns of op(B): tB = 0 -> B[k][j]; tB = 1 -> B[j][k]
-    k_oz_split<<<dim3((n + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, n, np, g.tB ? n : 1,
-                                                       g.tB ? 1 : n, nullptr, 0, 0, Bs, sl, exB, n);
+    k_oz_split<<<dim3((rowsB + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, n, kTN,
+                                                          g.tB ? n : 1, g.tB ? 1 : n, nullptr, 0, 0,
+                                                          Bs, slB, exB, n);
     OzMmaArgs m;
-    m.As = As; m.sAs = sl; m.exA = exA; m.sExA = n;
-    m.Bs = Bs; m.sBs = sl; m.exB = exB; m.sExB = n;
+    m.As = As; m.sAs = slA; m.exA = exA; m.sExA = n;
+    m.Bs = Bs; m.sBs = slB; m.exB = exB; m.sExB = n;
     m.C = g.C + b0 * g.sC; m.sC = g.sC;
-    m.n = n; m.np = np;
+    m.n = n;
     m.rs = g.rs ? g.rs + b0 * g.srs : nullptr; m.srs = g.srs; m.rs_mode = g.rs ? g.rs_mode : 0;
     m.cs = g.cs ? g.cs + b0 * g.scs : nullptr; m.scs = g.scs; m.cs_mode = g.cs ? g.cs_mode : 0;
     m.alpha = g.alpha; m.beta = g.beta;

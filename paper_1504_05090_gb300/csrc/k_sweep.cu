@@ -10,6 +10,8 @@
 //   G' = G - (Delta/R) (I - G) e_i e_i^T G.
 // Only spin up is evolved: on the bipartite half-filled lattice
 // G_dn = I - P G_up^T P (P = diag((-1)^{x+y})), so G_dn,ii = 1 - G_up,ii.
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -98,9 +100,10 @@ __device__ __forceinline__ df32 sm_coef(const MetroArgs& a, int s, df32 g) {
   return -(du * y);
 }
 
+// Column j of G, rows ra .. rb-1: G += U V^T over the cnt pending updates.
 template <typename T>
 __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int cnt, int N, int NP,
-                                              int j) {
+                                              int j, int ra, int rb) {
   if (j >= N) return;
   T v[kMaxDelay];
 #pragma unroll
@@ -110,29 +113,107 @@ __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int 
   constexpr int RB = 8;
   T cur[RB], nxt[RB];
 #pragma unroll
-  for (int q = 0; q < RB; ++q) cur[q] = (q < N) ? G[static_cast<size_t>(q) * N + j] : T(0);
-  for (int r0 = 0; r0 < N; r0 += RB) {
+  for (int q = 0; q < RB; ++q) cur[q] = (ra + q < rb) ? G[static_cast<size_t>(ra + q) * N + j] : T(0);
+  for (int r0 = ra; r0 < rb; r0 += RB) {
     const int r1 = r0 + RB;
 #pragma unroll
     for (int q = 0; q < RB; ++q)
-      nxt[q] = (r1 + q < N) ? G[static_cast<size_t>(r1 + q) * N + j] : T(0);
+      nxt[q] = (r1 + q < rb) ? G[static_cast<size_t>(r1 + q) * N + j] : T(0);
 #pragma unroll
     for (int q = 0; q < RB; ++q) {
       ProdSum<T> acc;
 #pragma unroll
       for (int m = 0; m < kMaxDelay; ++m)
         if (m < cnt) acc.add(U[m * NP + r0 + q], v[m]);
-      if (r0 + q < N) G[static_cast<size_t>(r0 + q) * N + j] = cur[q] + acc.get();
+      if (r0 + q < rb) G[static_cast<size_t>(r0 + q) * N + j] = cur[q] + acc.get();
     }
 #pragma unroll
     for (int q = 0; q < RB; ++q) cur[q] = nxt[q];
   }
 }
 
+// Barrier between the cs CTAs of one chain's cluster around the flushes of G
+// (global memory).  Thread 0 arrives on every peer's mbarrier (release at
+// cluster scope) and waits for its own for at most 0.2 s; a wait that gives up
+// sets kDevTimeout and lets the CTA go on, so the kernel always ends.  The __threadfence pair makes the CTA's global writes visible before
+// the arrival and the peers' writes after the wait.  Barrier phases alternate
+// between two mbarriers: a peer can be at most one phase ahead (it cannot pass
+// phase f + 1 before this CTA arrived for it), so an arrival for phase f + 1
+// never lands on the mbarrier that still collects phase f.
+constexpr unsigned long long kPeerWaitNs = 200000000ull;  // 0.2 s of %globaltimer
+constexpr long long kPeerWaitPolls = 1LL << 24;             // and at most this many polls
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// `broken` (shared) is set once a wait gave up; later barriers of the launch
+// then only synchronise the CTA.
+__device__ __forceinline__ void peer_barrier(uint64_t* bars, int cs, int rank, int& phase,
+                                             int* status, int* broken) {
+  __syncthreads();
+  if (threadIdx.x == 0 && !*broken) {
+    __threadfence();
+    const uint32_t local = static_cast<uint32_t>(__cvta_generic_to_shared(bars + (phase & 1)));
+    for (int r = 0; r < cs; ++r) {
+      if (r == rank) continue;
+      uint32_t remote;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(r));
+      asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
+                   : "memory");
+    }
+    uint32_t done = 0;
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; it < kPeerWaitPolls && !done; ++it) {
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(local), "r"((phase >> 1) & 1)
+          : "memory");
+      if (!done && (it & 255) == 255 && global_ns() - t0 > kPeerWaitNs) break;
+    }
+    if (!done) {
+      atomicExch(status, kDevTimeout);
+      *broken = 1;
+    }
+    __threadfence();
+  }
+  ++phase;
+  __syncthreads();
+}
+
+// Thread-block cluster of cs CTAs per chain (cs = 1: one CTA).  Every CTA
+// takes the same site decisions and builds the same U, V from the same data
+// (identical instruction streams, so identical results); in a flush each CTA
+// adds U V^T to its own block of N / cs rows of G.  Two peer barriers bracket
+// every flush: no CTA overwrites rows that a peer may still read for the
+// sites before the flush, and every CTA reads the new rows after it.
 template <typename T>
 __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, MetroArgs a) {
-  const int c = blockIdx.x;
+  const int cs = a.cs;
+  const int c = blockIdx.x / cs;
+  const int rank = blockIdx.x - c * cs;  // cluster rank (the cluster spans blockIdx.x)
   const int N = a.N;
+  const int ra = (rank * N) / cs, rb = ((rank + 1) * N) / cs;
+  __shared__ uint64_t xbar[2];
+  __shared__ int xbroken;
+  int xphase = 0;
+  if (cs > 1) {
+    if (threadIdx.x == 0) {
+      // a peer wait of an earlier launch gave up: results are void already,
+      // so this launch does not wait again
+      xbroken = (*reinterpret_cast<volatile int*>(a.status) == kDevTimeout);
+      for (int b = 0; b < 2; ++b)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(
+                         static_cast<uint32_t>(__cvta_generic_to_shared(xbar + b))),
+                     "r"(cs - 1));
+      asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    cooperative_groups::this_cluster().sync();
+  }
   const int NP = blockDim.x;
   const int j = threadIdx.x;
   const int lane = j & 31;
@@ -175,6 +256,9 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
   }
   int cnt = 0;
   unsigned naccept = 0;
+  // The field is written back after the slice: a peer CTA of the cluster may
+  // still be reading the slice's initial field when this one accepts a flip.
+  bool flip = false;
   for (int i = 0; i < N; ++i) {
     const T colv = pc[0], rowv = pr[0];
 #pragma unroll
@@ -229,15 +313,19 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
           d[j] = dj;
           df[j] = to_f32(dj);
         } else if (j == i) {
-          s_l[i] = static_cast<int8_t>(-ss[i]);
+          flip = true;
         }
       }
       __syncthreads();
       ++cnt;
       if (cnt == a.k) {
-        delayed_flush(G, U, V, cnt, N, NP, j);
+        if (cs > 1) peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
+        delayed_flush(G, U, V, cnt, N, NP, j, ra, rb);
         cnt = 0;
-        __syncthreads();
+        if (cs > 1)
+          peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
+        else
+          __syncthreads();
 #pragma unroll
         for (int q = 0; q < kPre; ++q) {
           const int ii = i + 1 + q;
@@ -247,8 +335,17 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
       }
     }
   }
-  if (cnt > 0) delayed_flush(G, U, V, cnt, N, NP, j);
-  if (j == 0) a.accepted[c] += naccept;
+  if (cnt > 0) {
+    if (cs > 1) peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
+    delayed_flush(G, U, V, cnt, N, NP, j, ra, rb);
+  }
+  // No CTA leaves while a peer may still arrive on its barrier or read the
+  // slice's field.
+  if (cs > 1) cooperative_groups::this_cluster().sync();
+  if (rank == 0) {
+    if (flip) s_l[j] = static_cast<int8_t>(-ss[j]);
+    if (j == 0) a.accepted[c] += naccept;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -545,8 +642,23 @@ cudaError_t launch_metropolis(T* G, int8_t* field, int C, const MetroArgs& a, cu
   cudaError_t e = cudaFuncSetAttribute(k_metropolis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm));
   if (e != cudaSuccess) return e;
-  k_metropolis<T><<<C, NP, sm, st>>>(G, field, a);
-  return cudaGetLastError();
+  if (a.cs <= 1) {
+    k_metropolis<T><<<C, NP, sm, st>>>(G, field, a);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * a.cs, 1, 1);
+  cfg.blockDim = dim3(NP, 1, 1);
+  cfg.dynamicSmemBytes = sm;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = a.cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_metropolis<T>, G, field, a);
 }
 
 template <typename T>

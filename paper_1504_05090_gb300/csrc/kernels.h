@@ -18,6 +18,8 @@ struct MetroArgs {
   double em2, ep2;            // exp(-2 lambda) - 1, exp(+2 lambda) - 1
   float em2h, em2l, ep2h, ep2l;  // the same as float pairs (hi + lo)
   unsigned long long* accepted;
+  int cs;       // CTAs per chain (thread-block cluster of cs, 1 = no cluster)
+  int* status;  // device status word (kDevTimeout if a peer wait gave up)
 };
 
 struct KronArgs {

@@ -142,6 +142,33 @@ def test_uneven_batch_of_six_lattices_matches_oracle():
                 chain += 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "df32"])
+def test_metropolis_split_over_a_cluster_is_invisible(prec):
+    """One, two and four CTAs per chain (each folding the delayed update into
+    its own rows of G, peer barriers around every flush) give bit-identical
+    fields, G, acceptance counts and observables."""
+    groups = [_grp(8, 8, U=3.0, beta=2.0, dtau=0.125, ns=5, k=16, C=3, prec=prec),
+              _grp(6, 4, U=2.0, beta=1.0, dtau=0.25, ns=2, k=4, C=2, prec=prec)]
+    sims = []
+    try:
+        for cs in (1, 2, 4):
+            sim = _sim(groups, seed=21)
+            sim.set_metropolis_split(cs)
+            sim.sweep(2, measure=True)
+            sims.append(sim)
+        ref = sims[0]
+        for sim in sims[1:]:
+            for fa, fb in zip(sim.field(), ref.field()):
+                assert np.array_equal(fa, fb)
+            for c in range(5):
+                assert np.array_equal(sim.G(c, 0), ref.G(c, 0))
+            assert np.array_equal(sim.stats()[1], ref.stats()[1])
+            np.testing.assert_array_equal(sim.observables(), ref.observables())
+    finally:
+        for sim in sims:
+            sim.close()
+
+
 def test_autotuner_respects_the_drift_target():
     import paper_1504_05090_gb300 as pkg
     g = _grp(4, 4, U=2.0, beta=10.0, dtau=0.125, ns=10, k=8, C=4)
@@ -267,12 +294,17 @@ def test_tensor_core_fp64_products_match_fp64_pipe():
     """Digit-sliced tcgen05 products (default for N >= 64) against the FP64
     pipe on the same fields: G(0), G(tau) and the gradient agree to 1e-12."""
     g = _grp(16, 16, U=2.0, beta=10.0, dtau=0.125, ns=10, C=2)
+    # N = 144 and 140: the last row tile (128 / 64 rows) and the last K chunk
+    # (32) are partly padding
+    g12 = _grp(12, 12, U=3.0, beta=4.0, dtau=0.125, ns=8, C=1)
+    g14 = _grp(14, 10, U=1.0, beta=3.0, dtau=0.1, ns=6, C=1)
     gs = _grp(6, 6, U=2.0, beta=2.0, dtau=0.1, ns=5, C=1)  # N = 36: always the FP64 pipe
-    with _sim([g, gs], seed=5) as a, _sim([g, gs], seed=5) as b:
+    groups = [g, g12, g14, gs]
+    with _sim(groups, seed=5) as a, _sim(groups, seed=5) as b:
         b.set_gemm_mode("fp64")
         a.recompute_G()
         b.recompute_G()
-        for c in range(3):
+        for c in range(5):
             assert _rel(a.G(c, 0), b.G(c, 0)) < 1e-12
         ga, gb = a.gtau(), b.gtau()
         for x, y in zip(ga, gb):
