@@ -186,9 +186,11 @@ int64_t dqmc_launch_count(const dqmc_ctx* ctx);
  * updates, the split-D Green-function formula, G(tau) at stabilisation
  * points), N >= 64 only:
  *   DQMC_GEMM_TENSOR (default): tcgen05 tensor cores, each FP64 row/column
- *     cut into eight exponent-aligned 7-bit digits (BF16 operands, exact FP32
- *     accumulation of digit products, FP64 recombination); agrees with FP64
- *     products to rounding level.
+ *     cut into eight exponent-aligned 7-bit digits (BF16 operands, FP32
+ *     accumulation of digit products, exact integer recombination); the
+ *     error of an element is below about 2^-53 max_k|a_ik| max_k|b_kj|.
+ *     The library arranges the scaled products of the stabilisation so that
+ *     this matches the FP64 result to rounding level.
  *   DQMC_GEMM_FP64: the FP64 pipe.
  * Smaller clusters always use the FP64 pipe.  Errors: DQMC_ERR_ARG. */
 #define DQMC_GEMM_TENSOR 0

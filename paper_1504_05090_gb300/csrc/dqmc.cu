@@ -295,6 +295,7 @@ int stack_right(dqmc_ctx* ctx, Group& g, int j) {
                                     g.N, g.C, ctx->d_status, g.st));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
+  m.balance = 1;  // the rows of T differ in magnitude; Rtil is triangular
   m.B = g.RT + (j - 1) * g.nn(); m.sB = g.sstride();
   m.C = g.RT + j * g.nn(); m.sC = g.sstride();
   DQ_CLASS(ctx, kTGemm);
@@ -320,6 +321,7 @@ int stack_left(dqmc_ctx* ctx, Group& g, int j) {
                                     g.N, g.C, ctx->d_status, g.st));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
+  m.balance = 1;  // the rows of T differ in magnitude; Rtil is triangular
   m.B = g.LT + (j + 1) * g.nn(); m.sB = g.sstride();
   m.C = g.LT + j * g.nn(); m.sC = g.sstride();
   DQ_CLASS(ctx, kTGemm);
@@ -342,6 +344,7 @@ int form_mid(dqmc_ctx* ctx, Group& g, int j0, long long es, int batch, double* o
   DQ_LAUNCH(ctx, gemm(ctx, g, m, batch));
   m.A = g.RT + j0 * g.nn();
   m.B = g.LT + j0 * g.nn();
+  m.balance = 1;
   m.rs_mode = 3;
   m.cs_mode = 3;
   m.beta = 1.0;
@@ -356,9 +359,13 @@ int recompute(dqmc_ctx* ctx, Group& g, int j) {
   DQ_CLASS(ctx, kTInverse);
   DQ_LAUNCH(ctx, launch_gj_cluster(g.X, g.nn(), g.G64, g.nn(), g.N, g.C, nullptr, ctx->d_status,
                                    g.st));
+  // U_L (Db_L^{-1} Mid^{-1}): Mid^{-1} grows like Db_L along its rows, so the
+  // scale is folded into them (Db_L^{-1} Mid^{-1} Db_R^{-1} is O(|G|)).
   GemmArgs m = gemm0(g.N);
   m.A = g.LU + j * g.nn(); m.sA = g.sstride(); m.tA = 1;
   m.ks = g.LD + j * g.N; m.sks = static_cast<long long>(g.nc + 1) * g.N; m.ks_mode = 2;
+  m.ks_on_b = 1;
+  m.balance = 1;
   m.B = g.G64; m.sB = g.nn();
   m.C = g.Rtil; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);
@@ -520,6 +527,8 @@ int all_points_w1(dqmc_ctx* ctx, Group& g) {
   GemmArgs m = gemm0(g.N);
   m.A = g.LU; m.sA = g.nn(); m.tA = 1;
   m.ks = g.LD; m.sks = g.N; m.ks_mode = 2;
+  m.ks_on_b = 1;  // as in recompute: the scale goes with the rows of Mid^{-1}
+  m.balance = 1;
   m.B = g.A2; m.sB = g.nn();
   m.C = g.W1; m.sC = g.nn();
   DQ_CLASS(ctx, kTGemm);

@@ -1,19 +1,26 @@
-// FP64 matrix products on the tcgen05 tensor cores (BF16 x BF16 -> FP32),
-// exact to FP64 rounding level, for the stabilisation GEMMs of the UDV chain
-// (Sec. 2: the O(Lambda N^3) matrix work behind Eq. (3) and G_ij(tau_l)).
+// FP64 matrix products on the tcgen05 tensor cores (BF16 x BF16 -> FP32)
+// for the stabilisation GEMMs of the UDV chain (Sec. 2: the O(Lambda N^3)
+// matrix work behind Eq. (3) and G_ij(tau_l)).
 //
 // On GB300 the FP64 pipe issues 1.2 TFLOP/s, the BF16 tensor cores 2.25
-// PFLOP/s.  Each FP64 row of op(A) diag(ks) (and column of op(B)) is written
-// as x = 2^e sum_{p<8} a_p 2^{-7p} with signed 7-bit integers a_p, where e is
+// PFLOP/s.  Each FP64 row of op(A) (and column of op(B)), with the optional
+// inner scale folded into one of the two, is written as
+// x = 2^e sum_{p<8} a_p 2^{-7p} with signed 7-bit integers a_p, where e is
 // fixed per row (column) by its largest element: the 53-bit significand of
 // every element is aligned to that exponent with integer shifts and cut into
-// eight 7-bit digits.  Digits are exact in BF16, products of two digits need
-// 14 bits, and a sum of 256 of them fits the 24-bit FP32 significand, so every
-// digit product A_p B_q is exact in the FP32 accumulator.  The products with
-// p + q = d (d = 0..7) share one TMEM accumulator; the eight accumulators are
-// combined in FP64 in the epilogue:
+// eight 7-bit digits.  Digits are exact in BF16 and products of two digits
+// need 14 bits.  The products with p + q = d (d = 0..7) share one TMEM
+// accumulator P_d; a sum of up to 2^24 / 127^2 = 1040 digit products is exact
+// in FP32, which covers every accumulator with d <= 3 for K <= 256; the
+// higher ones (weights 2^-28 and below) stay exact unless their digits are
+// systematically near 127.  The epilogue combines the accumulators exactly in
+// 64-bit integers:
 //   C_ij = alpha rs_i cs_j 2^{e_i + f_j} sum_d 2^{-7d} P_d,ij + beta C_ij.
-// Digits beyond p + q = 7 are below 2^-56 relative and dropped.
+// Digits beyond p + q = 7 are below 2^-56 of the row-times-column scale and
+// dropped.  Accuracy is therefore relative to max_k |a_ik| max_k |b_kj|, not
+// to sum_k |a_ik b_kj| as in an FP64 GEMM: a product in which op(A)'s row is
+// small where op(B)'s column is large (opposite grading along k) loses the
+// small entries; callers place the inner scale so that this does not occur.
 //
 // Tile: one CTA computes 128 x 64 of C for one matrix, K streamed in chunks of
 // 32.  The split kernel writes the digit slices tile-blocked, each (slice, row
@@ -64,20 +71,55 @@ __device__ __forceinline__ double oz_scale(const double* p, int mode, int i) {
   }
 }
 
+// Inner-index balance: kexp[k] = unbiased exponent of max_j |op(B)_kj s_k|
+// (s the inner scale when it goes with op(B)), 0 for a zero row.  Integer
+// work only.  One warp per k.
+__global__ void __launch_bounds__(256) k_oz_kexp(const double* Mall, long long sM, int n,
+                                                long long sv, long long sk, const double* ksall,
+                                                long long sks, int ks_mode, int* kexpall) {
+  const int b = blockIdx.y;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (k >= n) return;
+  const double* M = Mall + b * sM;
+  int emax = -1;
+  for (int j = lane; j < n; j += 32)
+    emax = max(emax, static_cast<int>((__double_as_longlong(M[j * sv + k * sk]) >> 52) & 0x7FF));
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
+  if (lane == 0) {
+    int e = 0;
+    if (emax > 0) {
+      e = emax - 1023;
+      if (ks_mode != 0 && ksall) {
+        const double sc = oz_scale(ksall + b * sks, ks_mode, k);
+        const int Es = static_cast<int>((__double_as_longlong(sc) >> 52) & 0x7FF);
+        if (Es > 0) e += Es - 1023;
+      }
+    }
+    kexpall[b * static_cast<long long>(n) + k] = e;
+  }
+}
+
 // One warp per vector v of the batch entry: element k of vector v is
-// M[v sv + k sk] (times the inner scale of k).  Writes the 8 digit slices in
-// the tile-blocked layout (rows padded to a multiple of R, K to a multiple of
-// the chunk, zero padding) and the scale exponent ex[v].
+// M[v sv + k sk] (times the inner scale of k, times 2^{ksign kexp[k]} when
+// balancing; the power of two only moves the digit alignment, as an integer
+// exponent offset).  Writes the 8 digit slices in the tile-blocked layout
+// (rows padded to a multiple of R, K to a multiple of the chunk, zero
+// padding) and the scale exponent ex[v].
 __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long sM, int n, int R,
                                                  long long sv, long long sk, const double* ksall,
-                                                 long long sks, int ks_mode, __nv_bfloat16* outall,
-                                                 long long sOut, int* exall, long long sEx) {
+                                                 long long sks, int ks_mode, const int* kexpall,
+                                                 int ksign, __nv_bfloat16* outall, long long sOut,
+                                                 int* exall, long long sEx) {
   const int nrt = (n + R - 1) / R, nkc = (n + kTK - 1) / kTK, np = nkc * kTK;
   const int b = blockIdx.y;
   const double* M = Mall + b * sM;
   __shared__ double ksv[kMaxN];
+  __shared__ int kev[kMaxN];
   const double* ks = ksall ? ksall + b * sks : nullptr;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) ksv[k] = oz_scale(ks, ks_mode, k);
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    ksv[k] = oz_scale(ks, ks_mode, k);
+    kev[k] = kexpall ? ksign * kexpall[b * static_cast<long long>(n) + k] : 0;
+  }
   __syncthreads();
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (v >= nrt * R) return;
@@ -87,11 +129,11 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
       for (int p = 0; p < kS; ++p) out[oz_offset(p, v, k, R, nrt, nkc)] = __float2bfloat16_rn(0.0f);
     return;
   }
-  int emax = -2000;
+  int emax = -100000;
   for (int k = lane; k < n; k += 32) {
     const double x = (ks_mode != 0) ? M[v * sv + k * sk] * ksv[k] : M[v * sv + k * sk];
     const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
-    if (E != 0) emax = max(emax, E - 1023);
+    if (E != 0) emax = max(emax, E - 1023 + kev[k]);
   }
   for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
   if (lane == 0) exall[b * sEx + v] = emax - 6;
@@ -105,7 +147,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
       if (E != 0) {  // zero and subnormal inputs contribute zero digits
         const unsigned long long mant =
             (static_cast<unsigned long long>(bits) & ((1ULL << 52) - 1)) | (1ULL << 52);
-        const int sh = emax - (E - 1023);
+        const int sh = emax - (E - 1023 + kev[k]);
         al = (sh < 64) ? (mant >> sh) : 0ULL;
       }
       sg = (bits < 0) ? -1.0f : 1.0f;
@@ -197,6 +239,7 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   __shared__ uint64_t full[kStages], mmad[kStages];
   __shared__ uint32_t tmem_sh;
   __shared__ int fail_sh;
+  __shared__ double colf[kTN];  // cs_j 2^{f_j - 21} of this CTA's columns
   const int b = blockIdx.z;
   const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * kTN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -204,6 +247,12 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   const int nrtA = (n + kTM - 1) / kTM, nrtB = (n + kTN - 1) / kTN, nkc = (n + kTK - 1) / kTK;
   const __nv_bfloat16* As = a.As + b * a.sAs;
   const __nv_bfloat16* Bs = a.Bs + b * a.sBs;
+  if (threadIdx.x >= 64) {
+    const int q = threadIdx.x - 64, j = j0 + q;
+    colf[q] = (j < n) ? oz_scale(a.cs ? a.cs + b * a.scs : nullptr, a.cs_mode, j) *
+                            ldexp(1.0, a.exB[b * a.sExB + j] - 21)
+                      : 0.0;
+  }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_sh)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -285,38 +334,47 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   if (!ok && threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
+    // Recombination.  Every accumulator holds an integer P_d (a sum of digit
+    // products); sum_d P_d 2^{-7d} = 2^{-21} (hi + 2^{-28} lo) with the exact
+    // 64-bit integers hi = sum_{d<4} P_d 2^{7(3-d)} and lo = sum_{d>=4} P_d
+    // 2^{7(7-d)} (both below 2^47, so exact in FP64): two conversions and one
+    // FMA in FP64 per element, the scales from per-row / per-column factors.
     const int i = i0 + warp * 32 + lane;
     const bool row_ok = i < n;
-    const double rsi = row_ok ? a.alpha * oz_scale(a.rs ? a.rs + b * a.srs : nullptr, a.rs_mode, i) : 0.0;
-    const int ei = row_ok ? a.exA[b * a.sExA + i] : 0;
+    const double rowf =
+        row_ok ? a.alpha * oz_scale(a.rs ? a.rs + b * a.srs : nullptr, a.rs_mode, i) *
+                     ldexp(1.0, a.exA[b * a.sExA + i])
+               : 0.0;
     double* C = a.C + b * a.sC;
-    const double* cs = a.cs ? a.cs + b * a.scs : nullptr;
     for (int c = 0; c < kTN / 16; ++c) {
-      double acc[16];
+      uint32_t v[kS][16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = 0.0;
       for (int d = 0; d < kS; ++d) {
-        uint32_t v[16];
         const uint32_t ta = tbase + (static_cast<uint32_t>(warp * 32) << 16) + d * kTN + c * 16;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+              "=r"(v[d][6]), "=r"(v[d][7]), "=r"(v[d][8]), "=r"(v[d][9]), "=r"(v[d][10]), "=r"(v[d][11]),
+              "=r"(v[d][12]), "=r"(v[d][13]), "=r"(v[d][14]), "=r"(v[d][15])
             : "r"(ta));
-        asm volatile("tcgen05.wait::ld.sync.aligned;");
-        const double w = ldexp(1.0, -7 * d);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = fma(static_cast<double>(__uint_as_float(v[q])), w, acc[q]);
       }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row_ok) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const int j = j0 + c * 16 + q;
+          const int jj = c * 16 + q, j = j0 + jj;
           if (j < n) {
-            const double sc = rsi * oz_scale(cs, a.cs_mode, j);
-            double val = sc * ldexp(acc[q], ei + a.exB[b * a.sExB + j]);
+            long long hi = 0, lo = 0;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+              hi += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (3 - d));
+#pragma unroll
+            for (int d = 4; d < kS; ++d)
+              lo += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (7 - d));
+            const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
+            double val = (sum * rowf) * colf[jj];
             const size_t o = static_cast<size_t>(i) * n + j;
-            if (a.beta != 0.0) val += a.beta * C[o];
+            if (a.beta != 0.0) val = fma(a.beta, C[o], val);
             C[o] = val;
           }
         }
@@ -337,7 +395,7 @@ static size_t oz_slice_elems(int n, int R) {
 
 size_t ozaki_scratch_bytes(int n, int max_batch) {
   return static_cast<size_t>(max_batch) *
-             ((oz_slice_elems(n, kTM) + oz_slice_elems(n, kTN)) * 2 + 2ull * n * sizeof(int)) +
+             ((oz_slice_elems(n, kTM) + oz_slice_elems(n, kTN)) * 2 + 3ull * n * sizeof(int)) +
          1024;
 }
 
@@ -351,19 +409,31 @@ cudaError_t launch_gemm_ozaki(const GemmArgs& g, int batch, void* scratch, int m
   __nv_bfloat16* Bs = As + slA * max_batch;
   int* exA = reinterpret_cast<int*>(Bs + slB * max_batch);
   int* exB = exA + static_cast<long long>(n) * max_batch;
+  int* kexp = exB + static_cast<long long>(n) * max_batch;
   cudaError_t e = cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
   if (e != cudaSuccess) return e;
   const int rowsA = (n + kTM - 1) / kTM * kTM, rowsB = (n + kTN - 1) / kTN * kTN;
   for (int b0 = 0; b0 < batch; b0 += max_batch) {
     const int nb = std::min(max_batch, batch - b0);
-    // rows of op(A) diag(ks): tA = 0 -> A[i][k]; tA = 1 -> A[k][i]
+    // The inner scale goes with op(A) (ks_on_b = 0) or with op(B).
+    const double* ks = g.ks ? g.ks + b0 * g.sks : nullptr;
+    const int ks_mode = g.ks ? g.ks_mode : 0;
+    const bool on_b = g.ks_on_b != 0;
+    // op(B) element (k, j): tB = 0 -> B[k][j]; tB = 1 -> B[j][k]
+    const long long bsv = g.tB ? n : 1, bsk = g.tB ? 1 : n;
+    if (g.balance)
+      k_oz_kexp<<<dim3((n + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, n, bsv, bsk,
+                                                       on_b ? ks : nullptr, g.sks,
+                                                       on_b ? ks_mode : 0, kexp);
+    const int* kx = g.balance ? kexp : nullptr;
+    // rows of op(A) [diag(ks)]: tA = 0 -> A[i][k]; tA = 1 -> A[k][i]
     k_oz_split<<<dim3((rowsA + 7) / 8, nb), 256, 0, st>>>(
-        g.A + b0 * g.sA, g.sA, n, kTM, g.tA ? 1 : n, g.tA ? n : 1,
-        g.ks ? g.ks + b0 * g.sks : nullptr, g.sks, g.ks ? g.ks_mode : 0, As, slA, exA, n);
-    // columns of op(B): tB = 0 -> B[k][j]; tB = 1 -> B[j][k]
-    k_oz_split<<<dim3((rowsB + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, n, kTN,
-                                                          g.tB ? n : 1, g.tB ? 1 : n, nullptr, 0, 0,
-                                                          Bs, slB, exB, n);
+        g.A + b0 * g.sA, g.sA, n, kTM, g.tA ? 1 : n, g.tA ? n : 1, on_b ? nullptr : ks, g.sks,
+        on_b ? 0 : ks_mode, kx, 1, As, slA, exA, n);
+    // columns of [diag(ks)] op(B)
+    k_oz_split<<<dim3((rowsB + 7) / 8, nb), 256, 0, st>>>(
+        g.B + b0 * g.sB, g.sB, n, kTN, bsv, bsk, on_b ? ks : nullptr, g.sks, on_b ? ks_mode : 0,
+        kx, -1, Bs, slB, exB, n);
     OzMmaArgs m;
     m.As = As; m.sAs = slA; m.exA = exA; m.sExA = n;
     m.Bs = Bs; m.sBs = slB; m.exB = exB; m.sExB = n;

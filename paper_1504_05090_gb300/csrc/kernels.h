@@ -53,6 +53,19 @@ struct GemmArgs {
   double* C; long long sC;
   const double* rs; long long srs; int rs_mode;
   const double* ks; long long sks; int ks_mode;
+  // The digit-sliced tensor-core path aligns the digits of every row of op(A)
+  // and every column of op(B) to that vector's largest element, so entries far
+  // below it lose bits.  ks_on_b = 1 folds the inner scale into the rows of
+  // op(B) instead of the columns of op(A): chosen where op(A) diag(ks) would
+  // be graded along k while op(B) grows to compensate.  The FP64 pipe forms
+  // a_ik ks_k b_kj either way.
+  int ks_on_b;
+  // balance = 1 (tensor path): before the split, the inner index k of both
+  // operands is rescaled by a power of two -- op(B)'s row k down to a largest
+  // entry of about 1, op(A)'s column k up by the same factor -- so that a row
+  // of op(A) aligns its digits to the terms that actually occur.  Used where
+  // the rows of op(B) differ in magnitude (triangular or UDV factors).
+  int balance;
   const double* cs; long long scs; int cs_mode;
   double alpha, beta;
 };
