@@ -62,6 +62,27 @@ __device__ __forceinline__ double wsum(double v) {
   return v;
 }
 
+// Warp sums of four values per lane with 6 FP64 additions instead of 20: the
+// first two butterfly stages exchange the halves each lane gives away, so a
+// lane carries 2, then 1 partial sum; afterwards lanes 8q .. 8q+7 hold the
+// sum of value q, which is scaled by `scale` and broadcast.
+__device__ __forceinline__ void wsum4(double (&a)[4], double scale) {
+  const int lane = threadIdx.x & 31;
+  const bool lo16 = lane < 16;
+  const double s0 = lo16 ? a[2] : a[0], s1 = lo16 ? a[3] : a[1];
+  const double k0 = lo16 ? a[0] : a[2], k1 = lo16 ? a[1] : a[3];
+  const double b0 = k0 + __shfl_xor_sync(0xFFFFFFFFu, s0, 16);
+  const double b1 = k1 + __shfl_xor_sync(0xFFFFFFFFu, s1, 16);
+  const bool hi8 = (lane & 8) != 0;
+  double c = (hi8 ? b1 : b0) + __shfl_xor_sync(0xFFFFFFFFu, hi8 ? b0 : b1, 8);
+  c += __shfl_xor_sync(0xFFFFFFFFu, c, 4);
+  c += __shfl_xor_sync(0xFFFFFFFFu, c, 2);
+  c += __shfl_xor_sync(0xFFFFFFFFu, c, 1);
+  c *= scale;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) a[q] = __shfl_sync(0xFFFFFFFFu, c, 8 * q);
+}
+
 __device__ double block_sum(double v, double* sbuf) {
   v = wsum(v);
   if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
@@ -117,8 +138,7 @@ __device__ __forceinline__ void reflect_owned(double* M, int n, int j, int c0, d
         for (int q = 0; q < 4; ++q) acc[q] = fma(vr, x[q][t], acc[q]);
       }
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[q] = wsum(acc[q]) * tau;
+    wsum4(acc, tau);
     double top[4];
 #pragma unroll
     for (int t = 0; t < kRPL; ++t) {
@@ -308,12 +328,13 @@ __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX,
       d = DBL_MIN;
     }
     if (threadIdx.x == 0) D[i] = d;
+    const double rd = 1.0 / d;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
       double v = 0.0;
       if (c > i)
-        v = X[static_cast<size_t>(c) * n + i] / d;
+        v = X[static_cast<size_t>(c) * n + i] * rd;
       else if (c == i)
-        v = betas[i] / d;
+        v = betas[i] * rd;
       Rt[static_cast<size_t>(i) * n + perm[c]] = v;
     }
   }
@@ -408,11 +429,15 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
 #pragma unroll
         for (int t = 0; t < kRPL; ++t)
           if (t == tk) fk = xv[h][t];
-        const double f = __shfl_sync(0xFFFFFFFFu, fk, lk);
+        const double nf = -__shfl_sync(0xFFFFFFFFu, fk, lk);
+        const double vk = nf * prow[k];  // new entry of the pivot column (one product per row)
 #pragma unroll
         for (int t = 0; t < kRPL; ++t) {
           const int jj = lane + 32 * t;
-          if (jj < n) Ai[jj] = (jj == k) ? -f * prow[k] : fma(-f, prow[jj], xv[h][t]);
+          if (jj < n) {
+            const double v = fma(nf, prow[jj], xv[h][t]);
+            Ai[jj] = (jj == k) ? vk : v;
+          }
         }
       }
     }
