@@ -49,12 +49,25 @@ __device__ int block_am(AM x, AM* sbuf, int* sres) {
   __syncthreads();
   if (threadIdx.x < 32) {
     const int nw = blockDim.x >> 5;
-    AM y = (static_cast<int>(threadIdx.x) < nw) ? sbuf[threadIdx.x] : AM{-1.0f, 1 << 30};
+    AM y = (static_cast<int>(threadIdx.x) < nw) ? sbuf[threadIdx.x] : AM{-3.0e38f, 1 << 30};
     y = warp_am(y);
     if (threadIdx.x == 0) *sres = y.i;
   }
   __syncthreads();
   return *sres;
+}
+
+// log2 |x| of a double in integer and FP32 arithmetic (exponent field plus
+// the FP32 log2 of the leading 23 mantissa bits): -2000 for zero and
+// subnormals, NaN for Inf/NaN.  Used for the pivoting norms, which only steer
+// the column order.
+__device__ __forceinline__ float log2_abs(double x) {
+  const long long bits = __double_as_longlong(x);
+  const int e = static_cast<int>((bits >> 52) & 0x7FF);
+  if (e == 0) return -2000.0f;
+  if (e == 0x7FF) return __int_as_float(0x7FC00000);
+  const float m = __int_as_float(0x3F800000 | static_cast<int>((bits >> 29) & 0x7FFFFF));
+  return static_cast<float>(e - 1023) + __log2f(m);
 }
 
 __device__ __forceinline__ double wsum(double v) {
@@ -83,36 +96,29 @@ __device__ __forceinline__ void wsum4(double (&a)[4], double scale) {
   for (int q = 0; q < 4; ++q) a[q] = __shfl_sync(0xFFFFFFFFu, c, 8 * q);
 }
 
-__device__ double block_sum(double v, double* sbuf) {
-  v = wsum(v);
-  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double y = (static_cast<int>(threadIdx.x) < static_cast<int>(blockDim.x >> 5)) ? sbuf[threadIdx.x] : 0.0;
-    y = wsum(y);
-    if (threadIdx.x == 0) sbuf[32] = y;
-  }
-  __syncthreads();
-  return sbuf[32];
-}
-
-// Apply I - tau v v^T (v = vsh[j..n), v_j = 1) to the rows M[c][j..n) for the
-// owned columns c = c0, c0 + CS, ... < n; four columns per warp at a time.
-// If vn1 != nullptr the partial column norms are downdated (column `pidx`
-// takes its input norm from position `jsrc`, see k_qrp_cluster).
+// Apply I - tau v v^T (v = vsh[j..n), v_j = 1) to the rows M[c][j..n) of
+// columns owned by this CTA, four columns per warp at a time.
+// The columns are cols[0 .. m) or, without a list, c0 + CS i (i < m).  If
+// ln1 != nullptr the partial column norms are downdated.  The norms
+// are kept as FP32 log2 values (ln1: current, ln2: at the last exact
+// recomputation); the downdate of LAPACK's xLAQP2,
+//   n1 <- n1 sqrt(1 - (|r|/n1)^2), recomputed when (1 - (|r|/n1)^2)(n1/n2)^2
+//   falls below sqrt(eps),
+// runs in that form on one lane.
 template <int CS>
-__device__ __forceinline__ void reflect_owned(double* M, int n, int j, int c0, double tau,
-                                              const double* vsh, double* vn1, double* vn2,
-                                              int pidx, int jsrc, double tol3z) {
+__device__ __forceinline__ void reflect_owned(double* M, int n, int j, const int* cols, int m,
+                                              int c0, double tau, const double* vsh, float* ln1,
+                                              float* ln2, float tol3z) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int m = (c0 < n) ? (n - c0 + CS - 1) / CS : 0;
   for (int g = w; 4 * g < m; g += nw) {
     int c[4];
     bool ok[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      ok[q] = (4 * g + q) < m;
-      c[q] = ok[q] ? c0 + CS * (4 * g + q) : c0;
+      const int idx = 4 * g + q;
+      ok[q] = idx < m;
+      const int ci = cols ? cols[ok[q] ? idx : 0] : c0 + CS * (ok[q] ? idx : 0);
+      c[q] = ci;
     }
     // All rows of the four columns are loaded before any arithmetic, so each
     // lane has up to 4 x kRPL independent loads in flight.
@@ -154,40 +160,38 @@ __device__ __forceinline__ void reflect_owned(double* M, int n, int j, int c0, d
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) top[q] = x[q][0];  // row j lives in lane 0, t = 0
-    if (vn1 == nullptr) continue;
-    // Downdate the partial norms (LAPACK xLAQP2); recompute on cancellation.
+    if (ln1 == nullptr) continue;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (!ok[q]) continue;
-      const int src = (c[q] == pidx) ? jsrc : c[q];
-      const double n1 = vn1[src], n2 = vn2[src];
-      double nn1 = n1, nn2 = n2;
-      // The downdated norm only guides pivoting, so its ratio arithmetic runs
-      // in FP32 on one lane (an exact recomputation follows on cancellation).
       int rec = 0;
-      if (lane == 0 && n1 != 0.0) {
-        float t = fabsf(static_cast<float>(top[q])) / static_cast<float>(n1);
-        t = fmaxf(0.0f, 1.0f - t * t);
-        const float qq = static_cast<float>(n1) / static_cast<float>(n2);
-        if (!(t * qq * qq > static_cast<float>(tol3z)))
-          rec = 1;
-        else
-          nn1 = n1 * static_cast<double>(sqrtf(t));
+      float nl1 = 0.0f, nl2 = 0.0f;
+      if (lane == 0) {
+        const float l1 = ln1[c[q]], l2 = ln2[c[q]];
+        nl1 = l1;
+        nl2 = l2;
+        if (l1 > -1000.0f) {
+          const float rt = log2_abs(top[q]) - l1;  // log2(|r| / n1)
+          const float t = fmaxf(0.0f, 1.0f - exp2f(2.0f * rt));
+          if (!(t * exp2f(2.0f * (l1 - l2)) > tol3z))
+            rec = 1;
+          else
+            nl1 = l1 + 0.5f * __log2f(t);
+        }
       }
-      const bool recompute = __shfl_sync(0xFFFFFFFFu, rec, 0) != 0;
-      if (recompute) {
+      if (__shfl_sync(0xFFFFFFFFu, rec, 0) != 0) {
         double s2 = 0.0;
         for (int r = j + 1 + lane; r < n; r += 32) {
           const double x = M[static_cast<size_t>(c[q]) * n + r];
-          s2 += x * x;
+          s2 = fma(x, x, s2);
         }
-        nn1 = sqrt(wsum(s2));
-        nn2 = nn1;
+        s2 = wsum(s2);
+        nl1 = nl2 = 0.5f * log2_abs(s2);
       }
       __syncwarp();
       if (lane == 0) {
-        vn1[c[q]] = nn1;
-        vn2[c[q]] = nn2;
+        ln1[c[q]] = nl1;
+        ln2[c[q]] = nl2;
       }
     }
   }
@@ -204,18 +208,24 @@ __device__ __forceinline__ int first_owned(int lo, int rank) {
 // ---------------------------------------------------------------------------
 // Householder QR with column pivoting of X^T (row c = column c of X), one
 // cluster of CS CTAs per matrix.  Outputs as k_qrp: Q^T, D = |diag R| and
-// Rtil = D^{-1} R P^T.  Column norms live in Vn ([batch][2 n]).  The
-// Householder vectors are parked in the Rtil buffer until Q is formed.
+// Rtil = D^{-1} R P^T.  The Householder vectors are parked in the Rtil buffer
+// until Q is formed.
 //
-// A column swap (j <-> p) moves the data of column j to position p without
-// touching the norm arrays: the owner of position p reads its input norm from
-// position j, which retires in the same step.  Two cluster barriers per step.
+// Pivoting is logical: a chosen column stays where it is and records its
+// step, each CTA keeps the columns it owns (c % CS == rank) that are still
+// live in a compact list and their partial norms (log2, FP32) in shared
+// memory.  After updating its columns a CTA publishes the best of them to
+// every CTA of the cluster (distributed shared memory, buffered by step
+// parity), so one cluster barrier per step orders both the column data in
+// global memory and the pivot candidates.  The head of a step (combining the
+// candidates, the reflector of the pivot column) runs in warp 0 of every CTA.
 // ---------------------------------------------------------------------------
 template <int CS>
 __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX, double* Qall,
                                                     long long sQ, double* Dall, long long sD,
                                                     double* Rall, long long sR, double* Vn, int n,
                                                     int* status) {
+  (void)Vn;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
   const int b = blockIdx.x / CS;
@@ -223,83 +233,93 @@ __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX,
   double* Qt = Qall + b * sQ;
   double* D = Dall + b * sD;
   double* Rt = Rall + b * sR;
-  double* vn1 = Vn + static_cast<size_t>(b) * 2 * n;
-  double* vn2 = vn1 + n;
   __shared__ double vsh[kMaxN], taus[kMaxN], betas[kMaxN];
-  __shared__ int perm[kMaxN];
-  __shared__ AM sred[32];
-  __shared__ int sres;
-  __shared__ double ssum[34];
+  __shared__ float ln1[kMaxN], ln2[kMaxN];  // log2 partial norms of the owned columns
+  __shared__ int stepof[kMaxN];             // step at which column c was chosen (n: not yet)
+  __shared__ int live[kMaxN], pos[kMaxN];   // owned live columns and their list positions
+  __shared__ int nlive;
+  __shared__ AM cand[2][CS];                // best live column of every CTA, by step parity
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double tol3z = 1.4901161193847656e-08;  // sqrt(DBL_EPSILON)
+  const float tol3z = 1.4901161193847656e-08f;  // sqrt(DBL_EPSILON)
 
   for (int c = rank + CS * w; c < n; c += CS * nw) {
     double s = 0.0;
     for (int r = lane; r < n; r += 32) {
       const double x = X[static_cast<size_t>(c) * n + r];
-      s += x * x;
+      s = fma(x, x, s);
     }
     s = wsum(s);
-    if (lane == 0) {
-      vn1[c] = sqrt(s);
-      vn2[c] = vn1[c];
-    }
+    if (lane == 0) ln1[c] = ln2[c] = 0.5f * log2_abs(s);
   }
-  for (int c = threadIdx.x; c < n; c += blockDim.x) perm[c] = c;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) stepof[c] = n;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int c = rank; c < n; c += CS) {
+      pos[c] = m;
+      live[m++] = c;
+    }
+    nlive = m;
+  }
+  __syncthreads();
+  // publish the best owned column for step 0 (warp 0)
+  auto publish = [&](int slot) {
+    AM m{-3.0e38f, n};
+    for (int i = lane; i < nlive; i += 32) m = am_combine(m, AM{ln1[live[i]], live[i]});
+    m = warp_am(m);
+    if (lane < CS) *cl.map_shared_rank(&cand[slot][rank], lane) = m;
+  };
+  if (w == 0) publish(0);
   cl.sync();
 
   for (int j = 0; j < n; ++j) {
-    AM m{-1.0f, n};
-    for (int c = j + threadIdx.x; c < n; c += blockDim.x)
-      m = am_combine(m, AM{static_cast<float>(vn1[c]), c});
-    int p = block_am(m, sred, &sres);
-    if (p < j || p >= n) {
-      if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
-      p = j;
-    }
-    if (p != j) {
-      if (rank == 0) {
-        for (int r = threadIdx.x; r < n; r += blockDim.x) {
-          const double t = X[static_cast<size_t>(j) * n + r];
-          X[static_cast<size_t>(j) * n + r] = X[static_cast<size_t>(p) * n + r];
-          X[static_cast<size_t>(p) * n + r] = t;
-        }
+    if (w == 0) {
+      // pivot: best candidate over the cluster (same order everywhere)
+      AM m{-3.0e38f, n};
+#pragma unroll
+      for (int r = 0; r < CS; ++r) m = am_combine(m, cand[j & 1][r]);
+      int p = m.i;
+      if (p < 0 || p >= n || stepof[p] != n) {  // no finite candidate: flag, take a free column
+        if (lane == 0) atomicExch(status, kDevNonFinite);
+        p = 0;
+        while (p < n - 1 && stepof[p] != n) ++p;
       }
-      if (threadIdx.x == 0) {
-        const int t = perm[j];
-        perm[j] = perm[p];
-        perm[p] = t;
-      }
-    }
-    cl.sync();
-    // Householder vector of column j (computed redundantly by every CTA).
-    const double* xj = X + static_cast<size_t>(j) * n;
-    double s = 0.0;
-    for (int r = j + 1 + threadIdx.x; r < n; r += blockDim.x) s += xj[r] * xj[r];
-    const double sig = block_sum(s, ssum);
-    if (threadIdx.x == 0) {  // reflector scalars: one thread, then broadcast
-      const double alpha = xj[j];
+      // reflector of column p (rows j .. n-1)
+      const double* xp = X + static_cast<size_t>(p) * n;
+      double sig = 0.0;
+      for (int r = j + 1 + lane; r < n; r += 32) sig = fma(xp[r], xp[r], sig);
+      sig = wsum(sig);
+      const double alpha = xp[j];
       double tau = 0.0, beta = alpha, scal = 1.0;
-      if (sig != 0.0) {
+      if (lane == 0 && sig != 0.0) {  // scalars on one lane, then broadcast
         const double nr = sqrt(alpha * alpha + sig);
         beta = (alpha <= 0.0) ? nr : -nr;
         tau = (beta - alpha) / beta;
         scal = 1.0 / (alpha - beta);
       }
-      taus[j] = tau;
-      betas[j] = beta;
-      ssum[33] = scal;
+      tau = __shfl_sync(0xFFFFFFFFu, tau, 0);
+      beta = __shfl_sync(0xFFFFFFFFu, beta, 0);
+      scal = __shfl_sync(0xFFFFFFFFu, scal, 0);
+      for (int r = j + lane; r < n; r += 32) {
+        const double v = (r == j) ? 1.0 : xp[r] * scal;
+        vsh[r] = v;
+        if (rank == 0 && r > j) Rt[static_cast<size_t>(j) * n + r] = v;
+      }
+      if (lane == 0) {
+        taus[j] = tau;
+        betas[j] = beta;
+        stepof[p] = j;
+        if (p % CS == rank) {  // drop p from the owned live list
+          const int at = pos[p], last = live[nlive - 1];
+          live[at] = last;
+          pos[last] = at;
+          --nlive;
+        }
+      }
     }
     __syncthreads();
-    const double scal = ssum[33];
-    const double tau = taus[j];
-    for (int r = j + threadIdx.x; r < n; r += blockDim.x) {
-      const double v = (r == j) ? 1.0 : xj[r] * scal;
-      vsh[r] = v;
-      if (rank == 0 && r > j) Rt[static_cast<size_t>(j) * n + r] = v;
-    }
+    reflect_owned<CS>(X, n, j, live, nlive, 0, taus[j], vsh, ln1, ln2, tol3z);
     __syncthreads();
-    reflect_owned<CS>(X, n, j, first_owned<CS>(j + 1, rank), tau, vsh, vn1, vn2, p, j, tol3z);
+    if (w == 0) publish((j + 1) & 1);
     cl.sync();
   }
 
@@ -313,14 +333,16 @@ __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX,
       vsh[r] = (r == j) ? 1.0 : Rt[static_cast<size_t>(j) * n + r];
     __syncthreads();
     const double tau = taus[j];
+    const int c0 = first_owned<CS>(j, rank);
     if (tau != 0.0)
-      reflect_owned<CS>(Qt, n, j, first_owned<CS>(j, rank), tau, vsh, nullptr, nullptr, -1, -1,
-                        tol3z);
+      reflect_owned<CS>(Qt, n, j, nullptr, (c0 < n) ? (n - c0 + CS - 1) / CS : 0, c0, tau, vsh,
+                        nullptr, nullptr, tol3z);
     __syncthreads();
   }
   cl.sync();  // every CTA is done with the Householder vectors in Rt
 
-  // D = |beta|, Rtil[i][perm[c]] = R[i][c] / D[i], R[i][c] = X[c][i] (c > i), R[i][i] = beta_i.
+  // D = |beta|; Rtil[i][c] = R[i][s] / D[i] with s = stepof[c] the pivot
+  // position of column c: R[i][s] = X[c][i] for s > i, beta_i for s = i.
   for (int i = rank; i < n; i += CS) {
     double d = absd(betas[i]);
     if (!(d > 0.0)) {
@@ -330,12 +352,13 @@ __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX,
     if (threadIdx.x == 0) D[i] = d;
     const double rd = 1.0 / d;
     for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const int sc = stepof[c];
       double v = 0.0;
-      if (c > i)
+      if (sc > i)
         v = X[static_cast<size_t>(c) * n + i] * rd;
-      else if (c == i)
+      else if (sc == i)
         v = betas[i] * rd;
-      Rt[static_cast<size_t>(i) * n + perm[c]] = v;
+      Rt[static_cast<size_t>(i) * n + c] = v;
     }
   }
 }
