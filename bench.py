@@ -195,6 +195,15 @@ def measured_peaks():
 FP64_PEAK = 152 * 2 * 2 * 2.07e9 / 1e12
 DF32_PEAK = 2 * 152 * 128 * 2.07e9 / 14 / 1e12
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the current kernel on the 64-chain 16x16 case, whose launches
+# do the same work as the benchmark's (one slice of 64 chains; 64 QRs of order
+# 256).  A kernel that changes after its capture drops out of this table.
+TRAFFIC = {
+    ("metropolis", "df32"): 33748224 + 768,   # 64 x 512 KB of G read once
+    ("qr_pivot", None): 39098112 + 53863168,  # X read, Q^T and Rtil written
+}
+
 
 def class_work(cls, acceptance, precision):
     """Algorithmic work of one sweep of the benchmark workload for a kernel
@@ -243,9 +252,10 @@ def roofline(profile, steps, acceptance, precision="df32"):
             peak, src = DF32_PEAK, "derived df32: FP32 pipe 152 x 128 FMA/clk x 2 x 2070 MHz / 14 instr"
         else:
             peak, src = 2 * 152 * 128 * 2.07e9 / 1e12, "derived FP32 pipe: 152 x 128 FMA/clk x 2 x 2070 MHz"
+        traffic = TRAFFIC.get((cls, precision), TRAFFIC.get((cls, None)))
         rows[cls] = {"bound": "tensor" if bound == "tensor" else "alu", "kernel": cls,
                      "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                     "traffic": None, "peak_source": src,
+                     "traffic": traffic, "peak_source": src,
                      "flops_per_launch": work * steps / n, "avg_launch_ms": ms / n, "launches": n}
     dom = max(profile.items(), key=lambda kv: kv[1][0])[0]
     return rows.get(dom, {"bound": "alu", "kernel": dom, "achieved": None, "peak": None,
