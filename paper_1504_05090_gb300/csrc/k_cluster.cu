@@ -42,21 +42,6 @@ __device__ __forceinline__ AM warp_am(AM x) {
   return x;
 }
 
-// Block-wide argmax; every thread gets the winning index.
-__device__ int block_am(AM x, AM* sbuf, int* sres) {
-  x = warp_am(x);
-  if ((threadIdx.x & 31) == 0) sbuf[threadIdx.x >> 5] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x >> 5;
-    AM y = (static_cast<int>(threadIdx.x) < nw) ? sbuf[threadIdx.x] : AM{-3.0e38f, 1 << 30};
-    y = warp_am(y);
-    if (threadIdx.x == 0) *sres = y.i;
-  }
-  __syncthreads();
-  return *sres;
-}
-
 // log2 |x| of a double in integer and FP32 arithmetic (exponent field plus
 // the FP32 log2 of the leading 23 mantissa bits): -2000 for zero and
 // subnormals, NaN for Inf/NaN.  Used for the pivoting norms, which only steer
@@ -368,9 +353,15 @@ __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX,
 // CTA (row % CS).  Pivot rows are chosen (partial pivoting over the rows not
 // yet used) but never moved; with pr[k] the pivot row of step k and ip its
 // inverse permutation, the in-place result Z gives A^{-1}[k][j] = Z[pr[k]][ip[j]],
-// written to Ainv at the end.  A is overwritten.  One cluster barrier per
-// step: the scaled pivot row is published by its owner one step late, after
-// the barrier, since no other CTA reads that row again.
+// written to Ainv at the end.  A is overwritten.
+//
+// One cluster barrier per step.  Within a step a CTA reads only its own rows
+// and the pivot row, which no CTA writes during the step (its scaled values
+// are written by the owner one step late, when no CTA reads that row any
+// more).  The pivot search therefore cannot look at a peer's rows: after its
+// elimination every CTA takes the largest |A[i][k+1]| over its own unused
+// rows and publishes it to every CTA of the cluster (distributed shared
+// memory, buffered by step parity), before the barrier.
 // ---------------------------------------------------------------------------
 template <int CS>
 __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, double* Iall,
@@ -384,13 +375,23 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
   __shared__ double prow[kMaxN], pend[kMaxN];
   __shared__ int pr[kMaxN], ip[kMaxN];
   __shared__ unsigned char used[kMaxN];
-  __shared__ AM sred[32];
-  __shared__ int sres;
+  __shared__ AM cand[2][CS];  // best unused owned row of every CTA for the next column
   __shared__ double sinv;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
   int pend_row = -1;  // owned pivot row whose scaled values wait in pend[]
   double la = 0.0;
   __syncthreads();
+  // warp 0: best |A[i][col]| over the owned unused rows, sent to every CTA
+  auto publish = [&](int col, int slot) {
+    AM m{-1.0f, n};
+    for (int i = rank + CS * lane; i < n; i += CS * 32)
+      if (!used[i]) m = am_combine(m, AM{static_cast<float>(absd(A[static_cast<size_t>(i) * n + col])), i});
+    m = warp_am(m);
+    if (lane < CS) *cl.map_shared_rank(&cand[slot][rank], lane) = m;
+  };
+  if (w == 0) publish(0, 0);
+  cl.sync();
   for (int k = 0; k < n; ++k) {
     if (pend_row >= 0) {
       for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
@@ -398,9 +399,9 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
       pend_row = -1;
     }
     AM m{-1.0f, n};
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (!used[i]) m = am_combine(m, AM{static_cast<float>(absd(A[static_cast<size_t>(i) * n + k])), i});
-    int p = block_am(m, sred, &sres);
+#pragma unroll
+    for (int r = 0; r < CS; ++r) m = am_combine(m, cand[k & 1][r]);
+    int p = m.i;
     if (p < 0 || p >= n || used[p]) {  // no finite pivot left: flag, take the first free row
       if (threadIdx.x == 0) atomicExch(status, kDevNonFinite);
       p = 0;
@@ -425,7 +426,6 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
       pr[k] = p;
     }
     // eliminate column k from the owned rows (the owned pivot row is only scaled)
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int kRPL = kMaxN / 32;
     const int tk = k >> 5, lk = k & 31;
     for (int i0 = rank + CS * w; i0 < n; i0 += 2 * CS * nw) {
@@ -465,6 +465,8 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
       }
     }
     if (p % CS == rank) pend_row = p;
+    __syncthreads();  // this CTA's eliminated rows and used[] are complete
+    if (w == 0 && k + 1 < n) publish(k + 1, (k + 1) & 1);
     cl.sync();
   }
   if (pend_row >= 0)
