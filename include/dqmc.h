@@ -108,10 +108,12 @@ int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure);
 
 /* Autotuner: for each group choose the stabilisation interval and the delay
  * depth for this GPU.  n_s: all candidates (L, 64, 48, ..., 3, 2 that are
- * <= L) run side by side in one probe context of 4 chains each; after two
- * warm-up sweeps the largest n_s whose G drift over three sweeps stays below
- * drift_target / 20 is taken (1 if none; the drift over many chains and
- * sweeps is heavy-tailed, hence the margin).  k: the fastest of 8, 16, 32 at that
+ * <= L and <= 64) run side by side in one probe context of 4 chains each;
+ * after two warm-up sweeps the largest n_s whose G drift over three sweeps
+ * stays below drift_target / 20 is taken (1 if none; the drift over many
+ * chains and sweeps is heavy-tailed, hence the margin).  If the probe reports
+ * non-finite values, the largest candidate is dropped and the rest probed
+ * again.  k: the fastest of 8, 16, 32 at that
  * n_s (8 chains, two timed sweeps).  out receives copies of groups with
  * stab_interval and delay_k replaced.  Creates and destroys its own contexts
  * on `stream`.  Errors: as dqmc_init. */

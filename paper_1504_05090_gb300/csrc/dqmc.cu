@@ -794,25 +794,41 @@ int dqmc_autotune(const dqmc_group* groups, int n_groups, double drift_target, u
   for (int gi = 0; gi < n_groups; ++gi) {
     const dqmc_group& g = groups[gi];
     const int L = static_cast<int>(std::llround(g.beta / g.dtau));
-    // Candidate stabilisation intervals, largest first; all probed at once.
+    // Candidate stabilisation intervals, largest first (at most 64 slices,
+    // beyond which the unstabilised B products lose all small scales); all
+    // probed at once, each as its own group.
     std::vector<int> cands;
     for (int ns : {L, 64, 48, 40, 32, 25, 20, 16, 12, 10, 8, 6, 5, 4, 3, 2})
-      if (ns <= L && ns >= 2 && (cands.empty() || ns < cands.back())) cands.push_back(ns);
+      if (ns <= L && ns <= 64 && ns >= 2 && (cands.empty() || ns < cands.back()))
+        cands.push_back(ns);
+    if (cands.empty()) cands.push_back(1);
     std::vector<dqmc_group> probe;
-    for (int ns : cands) {
-      dqmc_group p = g;
-      p.n_chains = std::min(g.n_chains, 4);
-      p.stab_interval = ns;
-      probe.push_back(p);
+    std::vector<double> drift;
+    int rc = DQMC_OK;
+    // A candidate so large that its G overflows sets the context's non-finite
+    // status for every probe; it is too large by definition, so the largest
+    // candidate is dropped and the rest probed again.
+    while (true) {
+      probe.clear();
+      for (int ns : cands) {
+        dqmc_group p = g;
+        p.n_chains = std::min(g.n_chains, 4);
+        p.stab_interval = ns;
+        probe.push_back(p);
+      }
+      dqmc_ctx* pc = nullptr;
+      rc = dqmc_init(probe.data(), static_cast<int>(probe.size()), seed, stream, &pc);
+      if (rc == DQMC_OK) {
+        rc = dqmc_sweep(pc, 2, 0);
+        if (rc == DQMC_OK) rc = dqmc_reset_stats(pc);
+        if (rc == DQMC_OK) rc = dqmc_sweep(pc, 3, 0);
+        drift.assign(pc->total, 0.0);
+        if (rc == DQMC_OK) rc = dqmc_get_stats(pc, drift.data(), nullptr);
+        dqmc_destroy(pc);
+      }
+      if (rc != DQMC_ERR_NAN || cands.size() <= 1) break;
+      cands.erase(cands.begin());
     }
-    dqmc_ctx* pc = nullptr;
-    DQ_RET(dqmc_init(probe.data(), static_cast<int>(probe.size()), seed, stream, &pc));
-    int rc = dqmc_sweep(pc, 2, 0);
-    if (rc == DQMC_OK) rc = dqmc_reset_stats(pc);
-    if (rc == DQMC_OK) rc = dqmc_sweep(pc, 3, 0);
-    std::vector<double> drift(pc->total);
-    if (rc == DQMC_OK) rc = dqmc_get_stats(pc, drift.data(), nullptr);
-    dqmc_destroy(pc);
     DQ_RET(rc);
     int chosen = 1;
     for (size_t c = 0; c < cands.size(); ++c) {
