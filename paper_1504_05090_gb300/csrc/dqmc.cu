@@ -260,6 +260,17 @@ int kron_nv(const Group& g, bool fp64) {
   return std::min(nv, g.N);
 }
 
+// Vectors per CTA of the slice wrap in the working precision.  The FP64
+// transforms are bound by the FP64 pipe and take large tiles; the float-pair
+// and FP32 ones run serial chains of compensated sums per element and need
+// many resident warps to hide their latency, hence small tiles (8 vectors,
+// about 35 KB of shared memory at N = 256: six CTAs per SM).
+template <typename T>
+int wrap_nv(const Group& g) {
+  if (sizeof(T) == 8 && !std::is_same<T, df32>::value) return kron_nv(g, true);
+  return std::min(8, g.N);
+}
+
 GemmArgs gemm0(int n) {
   GemmArgs a{};
   a.n = n;
@@ -470,9 +481,8 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
         break;
       }
   }
-  const bool fp64 = sizeof(T) == 8;
-  KronArgs wl = kron_base(g, kB, kron_nv(g, fp64));
-  KronArgs wr = kron_base(g, kBIT, kron_nv(g, fp64));
+  KronArgs wl = kron_base(g, kB, wrap_nv<T>(g));
+  KronArgs wr = kron_base(g, kBIT, wrap_nv<T>(g));
   wl.n_slices = wr.n_slices = 1;
   T* Gw = static_cast<T*>(g.Gw);
   int j = 1;
