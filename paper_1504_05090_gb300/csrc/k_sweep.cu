@@ -12,6 +12,8 @@
 // G_dn = I - P G_up^T P (P = diag((-1)^{x+y})), so G_dn,ii = 1 - G_up,ii.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -101,16 +103,20 @@ __device__ __forceinline__ df32 sm_coef(const MetroArgs& a, int s, df32 g) {
 }
 
 // Column j of G, rows ra .. rb-1: G += U V^T over the cnt pending updates.
-template <typename T>
+// MC = kMaxDelay keeps all of column j of V in registers for the whole flush;
+// a smaller MC reloads it in chunks of MC per row batch (fewer registers, the
+// same additions in the same order).
+template <typename T, int RB = 8, int MC = kMaxDelay>
 __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int cnt, int N, int NP,
                                               int j, int ra, int rb) {
   if (j >= N) return;
-  T v[kMaxDelay];
+  T v[MC];
+  if constexpr (MC == kMaxDelay) {
 #pragma unroll
-  for (int m = 0; m < kMaxDelay; ++m) v[m] = (m < cnt) ? V[m * NP + j] : T(0);
+    for (int m = 0; m < kMaxDelay; ++m) v[m] = (m < cnt) ? V[m * NP + j] : T(0);
+  }
   // Rows in batches of RB, the next batch loaded while the current one is
   // computed, so two batches of L2 loads are in flight per thread.
-  constexpr int RB = 8;
   T cur[RB], nxt[RB];
 #pragma unroll
   for (int q = 0; q < RB; ++q) cur[q] = (ra + q < rb) ? G[static_cast<size_t>(ra + q) * N + j] : T(0);
@@ -119,14 +125,22 @@ __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int 
 #pragma unroll
     for (int q = 0; q < RB; ++q)
       nxt[q] = (r1 + q < rb) ? G[static_cast<size_t>(r1 + q) * N + j] : T(0);
+    ProdSum<T> acc[RB];
+    for (int m0 = 0; m0 < cnt; m0 += MC) {
+      if constexpr (MC != kMaxDelay) {
 #pragma unroll
-    for (int q = 0; q < RB; ++q) {
-      ProdSum<T> acc;
+        for (int mm = 0; mm < MC; ++mm) v[mm] = (m0 + mm < cnt) ? V[(m0 + mm) * NP + j] : T(0);
+      }
 #pragma unroll
-      for (int m = 0; m < kMaxDelay; ++m)
-        if (m < cnt) acc.add(U[m * NP + r0 + q], v[m]);
-      if (r0 + q < rb) G[static_cast<size_t>(r0 + q) * N + j] = cur[q] + acc.get();
+      for (int q = 0; q < RB; ++q) {
+#pragma unroll
+        for (int mm = 0; mm < MC; ++mm)
+          if (m0 + mm < cnt) acc[q].add(U[(m0 + mm) * NP + r0 + q], v[mm]);
+      }
     }
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      if (r0 + q < rb) G[static_cast<size_t>(r0 + q) * N + j] = cur[q] + acc[q].get();
 #pragma unroll
     for (int q = 0; q < RB; ++q) cur[q] = nxt[q];
   }
@@ -185,6 +199,14 @@ __device__ __forceinline__ void peer_barrier(uint64_t* bars, int cs, int rank, i
   __syncthreads();
 }
 
+// Threads per column of G: two for float pairs (one computes the column and
+// one the row correction of an accepted flip, and they split the rows of the
+// flush), one otherwise.
+template <typename T>
+constexpr int metro_halves() {
+  return std::is_same<T, df32>::value ? 2 : 1;
+}
+
 // Thread-block cluster of cs CTAs per chain (cs = 1: one CTA).  Every CTA
 // takes the same site decisions and builds the same U, V from the same data
 // (identical instruction streams, so identical results); in a flush each CTA
@@ -192,12 +214,19 @@ __device__ __forceinline__ void peer_barrier(uint64_t* bars, int cs, int rank, i
 // every flush: no CTA overwrites rows that a peer may still read for the
 // sites before the flush, and every CTA reads the new rows after it.
 template <typename T>
-__global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, MetroArgs a) {
+__global__ void __launch_bounds__(256 * metro_halves<T>()) k_metropolis(T* Gall, int8_t* fieldall,
+                                                                      MetroArgs a) {
+  constexpr int kH = metro_halves<T>();
   const int cs = a.cs;
   const int c = blockIdx.x / cs;
   const int rank = blockIdx.x - c * cs;  // cluster rank (the cluster spans blockIdx.x)
   const int N = a.N;
-  const int ra = (rank * N) / cs, rb = ((rank + 1) * N) / cs;
+  const int NP = blockDim.x / kH;                // columns (N rounded up to a warp)
+  const int h = (kH == 2 && static_cast<int>(threadIdx.x) >= NP) ? 1 : 0;
+  // rows of G this thread folds the delayed updates into: the CTA's block of
+  // N / cs rows, split between the two halves when kH = 2
+  const int ra0 = (rank * N) / cs, rb0 = ((rank + 1) * N) / cs, rmid = ra0 + (rb0 - ra0 + 1) / 2;
+  const int ra = (kH == 2 && h) ? rmid : ra0, rb = (kH == 2 && !h) ? rmid : rb0;
   __shared__ uint64_t xbar[2];
   __shared__ int xbroken;
   int xphase = 0;
@@ -214,9 +243,8 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
     }
     cooperative_groups::this_cluster().sync();
   }
-  const int NP = blockDim.x;
-  const int j = threadIdx.x;
-  const int lane = j & 31;
+  const int j = threadIdx.x - h * NP;  // column of this thread
+  const int lane = threadIdx.x & 31;
   const bool act = j < N;
   T* G = Gall + static_cast<size_t>(c) * N * N;
   int8_t* s_l = fieldall + (static_cast<size_t>(c) * a.L + a.l0) * N;
@@ -231,7 +259,7 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
   int* ss = reinterpret_cast<int*>(df + NP);        // [NP] field of the slice
 
   const uint32_t sweep = *a.sweep_ctr;
-  if (act) {
+  if (act && h == 0) {
     const T gjj = G[static_cast<size_t>(j) * N + j];
     d[j] = gjj;
     df[j] = to_f32(gjj);
@@ -247,12 +275,22 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
 
   // Column i and row i of G for the next kPre sites, loaded ahead (a flush
   // rewrites G, after which the window is reloaded).
+  // With two threads per column each half keeps only its own vector (pr is
+  // then unused and stays empty).
   constexpr int kPre = 4;
-  T pc[kPre], pr[kPre];
+  T pc[kPre], pr[kH == 1 ? kPre : 1];
+  // G[j][q] for the column half (or single thread), G[q][j] for the row half
+  auto ld_c = [&](int q) -> T {
+    if (!act || q >= N) return T(0);
+    return (kH == 1 || h == 0) ? G[static_cast<size_t>(j) * N + q] : G[static_cast<size_t>(q) * N + j];
+  };
+  auto ld_r = [&](int q) -> T {
+    return (act && q < N) ? G[static_cast<size_t>(q) * N + j] : T(0);
+  };
 #pragma unroll
   for (int q = 0; q < kPre; ++q) {
-    pc[q] = (act && q < N) ? G[static_cast<size_t>(j) * N + q] : T(0);
-    pr[q] = (act && q < N) ? G[static_cast<size_t>(q) * N + j] : T(0);
+    pc[q] = ld_c(q);
+    if constexpr (kH == 1) pr[q] = ld_r(q);
   }
   int cnt = 0;
   unsigned naccept = 0;
@@ -260,15 +298,17 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
   // still be reading the slice's initial field when this one accepts a flip.
   bool flip = false;
   for (int i = 0; i < N; ++i) {
-    const T colv = pc[0], rowv = pr[0];
+    // kH == 2: colv is G[j][i] for h = 0 and G[i][j] for h = 1
+    const T colv = pc[0];
+    const T rowv = (kH == 1) ? pr[0] : pc[0];
 #pragma unroll
     for (int q = 0; q + 1 < kPre; ++q) {
       pc[q] = pc[q + 1];
-      pr[q] = pr[q + 1];
+      if constexpr (kH == 1) pr[q] = pr[q + 1];
     }
     const int inext = i + kPre;
-    pc[kPre - 1] = (act && inext < N) ? G[static_cast<size_t>(j) * N + inext] : T(0);
-    pr[kPre - 1] = (act && inext < N) ? G[static_cast<size_t>(inext) * N + j] : T(0);
+    pc[kPre - 1] = ld_c(inext);
+    if constexpr (kH == 1) pr[kPre - 1] = ld_r(inext);
     // Decision u < R_up R_dn with R_up = 1 + D_up (1 - G_ii), R_dn = 1 + D_dn G_ii
     // (G_dn,ii = 1 - G_up,ii).  Lane 0 of every warp takes it in FP32 unless u
     // lies within 1e-4 of R, where it is retaken in FP64; all warps agree
@@ -294,33 +334,60 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
     if (acc_i) {
       coef = shfl0(coef);
       ++naccept;
-      if (act) {
-        ProdSum<T> sc, sr;
-        for (int m = 0; m < cnt; ++m) {
-          sc.add(U[m * NP + j], V[m * NP + i]);
-          sr.add(U[m * NP + i], V[m * NP + j]);
+      if constexpr (kH == 1) {
+        if (act) {
+          ProdSum<T> sc, sr;
+          for (int m = 0; m < cnt; ++m) {
+            sc.add(U[m * NP + j], V[m * NP + i]);
+            sr.add(U[m * NP + i], V[m * NP + j]);
+          }
+          const T gc = colv + sc.get(), gr = rowv + sr.get();
+          const T uj = coef * ((j == i ? T(1) : T(0)) - gc);
+          U[cnt * NP + j] = uj;
+          V[cnt * NP + j] = gr;
+          // Only the diagonal of sites still to come (j > i) is updated.  Warps
+          // pass rejected sites without a barrier, so a slower warp may still be
+          // deciding an earlier site j <= i: its d[j], df[j] (dead for the rest
+          // of the slice) must keep the value every other warp decided with.
+          if (j > i) {
+            const T dj = d[j] + uj * gr;
+            d[j] = dj;
+            df[j] = to_f32(dj);
+          } else if (j == i) {
+            flip = true;
+          }
         }
-        const T gc = colv + sc.get(), gr = rowv + sr.get();
-        const T uj = coef * ((j == i ? T(1) : T(0)) - gc);
-        U[cnt * NP + j] = uj;
-        V[cnt * NP + j] = gr;
-        // Only the diagonal of sites still to come (j > i) is updated.  Warps
-        // pass rejected sites without a barrier, so a slower warp may still be
-        // deciding an earlier site j <= i: its d[j], df[j] (dead for the rest
-        // of the slice) must keep the value every other warp decided with.
-        if (j > i) {
-          const T dj = d[j] + uj * gr;
-          d[j] = dj;
-          df[j] = to_f32(dj);
-        } else if (j == i) {
-          flip = true;
+      } else {
+        // column correction (h = 0) and row correction (h = 1) of the flip
+        if (act) {
+          ProdSum<T> sa;
+          if (h == 0) {
+            for (int m = 0; m < cnt; ++m) sa.add(U[m * NP + j], V[m * NP + i]);
+            const T gc = colv + sa.get();
+            U[cnt * NP + j] = coef * ((j == i ? T(1) : T(0)) - gc);
+          } else {
+            for (int m = 0; m < cnt; ++m) sa.add(U[m * NP + i], V[m * NP + j]);
+            V[cnt * NP + j] = rowv + sa.get();
+          }
+        }
+        __syncthreads();
+        // every warp is at site i here, so the diagonal of the sites to come
+        // is updated before anyone decides the next site (barrier below)
+        if (act && h == 0) {
+          if (j > i) {
+            const T dj = d[j] + U[cnt * NP + j] * V[cnt * NP + j];
+            d[j] = dj;
+            df[j] = to_f32(dj);
+          } else if (j == i) {
+            flip = true;
+          }
         }
       }
       __syncthreads();
       ++cnt;
       if (cnt == a.k) {
         if (cs > 1) peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
-        delayed_flush(G, U, V, cnt, N, NP, j, ra, rb);
+        delayed_flush<T, 8 / kH, kMaxDelay / kH>(G, U, V, cnt, N, NP, j, ra, rb);
         cnt = 0;
         if (cs > 1)
           peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
@@ -328,23 +395,22 @@ __global__ void __launch_bounds__(256) k_metropolis(T* Gall, int8_t* fieldall, M
           __syncthreads();
 #pragma unroll
         for (int q = 0; q < kPre; ++q) {
-          const int ii = i + 1 + q;
-          pc[q] = (act && ii < N) ? G[static_cast<size_t>(j) * N + ii] : T(0);
-          pr[q] = (act && ii < N) ? G[static_cast<size_t>(ii) * N + j] : T(0);
+          pc[q] = ld_c(i + 1 + q);
+          if constexpr (kH == 1) pr[q] = ld_r(i + 1 + q);
         }
       }
     }
   }
   if (cnt > 0) {
     if (cs > 1) peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
-    delayed_flush(G, U, V, cnt, N, NP, j, ra, rb);
+    delayed_flush<T, 8 / kH, kMaxDelay / kH>(G, U, V, cnt, N, NP, j, ra, rb);
   }
   // No CTA leaves while a peer may still arrive on its barrier or read the
   // slice's field.
   if (cs > 1) cooperative_groups::this_cluster().sync();
   if (rank == 0) {
     if (flip) s_l[j] = static_cast<int8_t>(-ss[j]);
-    if (j == 0) a.accepted[c] += naccept;
+    if (threadIdx.x == 0) a.accepted[c] += naccept;
   }
 }
 
@@ -638,17 +704,18 @@ size_t metropolis_smem(int N, int k) {
 template <typename T>
 cudaError_t launch_metropolis(T* G, int8_t* field, int C, const MetroArgs& a, cudaStream_t st) {
   const int NP = ((a.N + 31) / 32) * 32;
+  const int threads = NP * metro_halves<T>();
   const size_t sm = metropolis_smem<T>(a.N, a.k);
   cudaError_t e = cudaFuncSetAttribute(k_metropolis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        static_cast<int>(sm));
   if (e != cudaSuccess) return e;
   if (a.cs <= 1) {
-    k_metropolis<T><<<C, NP, sm, st>>>(G, field, a);
+    k_metropolis<T><<<C, threads, sm, st>>>(G, field, a);
     return cudaGetLastError();
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C * a.cs, 1, 1);
-  cfg.blockDim = dim3(NP, 1, 1);
+  cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = sm;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
