@@ -225,8 +225,10 @@ def class_work(cls, acceptance, precision):
         return "alu64", C * (2 * nc + 1) * g3
     if cls in ("stack_kron", "gtau_propagate"):
         # two matrices (right and left stack; G(l,0) and Y) x L slices x N vectors
-        # x 2N(Lx+Ly) flops per Kronecker application
-        return "alu64", C * 2 * L * N * 2 * N * (Lx + Ly)
+        # x 2N(Lx+Ly) flops per Kronecker application; G(tau) is propagated in
+        # the working precision of float-pair groups
+        pair = cls == "gtau_propagate" and precision == "df32"
+        return ("alu32x2" if pair else "alu64"), C * 2 * L * N * 2 * N * (Lx + Ly)
     if cls == "metropolis":  # rank-1 Sherman-Morrison update per accepted flip
         return ("alu32x2" if precision == "df32" else "alu"), acceptance * C * N * L * 2.0 * N * N
     if cls == "wrap":  # B G B^-1 by Kronecker factors: 2 sides x N vectors x 2N(Lx+Ly)

@@ -132,12 +132,14 @@ int dqmc_use_graphs(dqmc_ctx* ctx, int on);
  * or NULL.  Synchronises. */
 int dqmc_recompute_G(dqmc_ctx* ctx, double* max_drift_out);
 
-/* Unequal-time Green function of the current field of every chain (Sec. 2,
- * "Green functions G_ij(tau_l) on a discrete imaginary-time grid"):
+/* Unequal-time Green function of the current field of every chain, on the
+ * Trotter grid tau_l = l dtau (Sec. 2, the G_ij(tau_l) the method produces):
  * out[chain][l][k] = 1/2 sum_sigma Re G_sigma,k(tau_l), l = 0..L, where
  * G_k = (1/N) sum_ij cos(k.(r_i - r_j)) G_ij(l,0), k = 2 pi (kx/Lx, ky/Ly)
- * with index kx + Lx*ky.  G(l,0) is formed stably at every stabilisation
- * point and propagated by B_l in between.  Row length per chain is
+ * with index kx + Lx*ky.  G(l,0) is formed stably (FP64) at every
+ * stabilisation point and propagated by B_l in between: in FP64, or in float
+ * pairs for groups with DQMC_DF32 working precision (agreeing to about 1e-9
+ * of the maximum).  Row length per chain is
  * (L_g + 1) * N_g of its group; dqmc_gtau_size() gives the total.
  * out: caller-owned doubles, on the device if out_on_device else on the host.
  * Requires current UDV stacks (true after dqmc_init, dqmc_sweep,

@@ -953,7 +953,10 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
                     cudaGetLastError()));
     GtauArgs ga{};
     ga.N = g.N; ga.Lx = g.p.Lx; ga.Ly = g.p.Ly; ga.L = g.L;
-    ga.nv = kron_nv(g, true);
+    // float-pair groups propagate in their working precision (small tiles,
+    // latency-bound like the wrap); FP64 and FP32 groups in FP64
+    const bool pair = g.p.precision == DQMC_DF32;
+    ga.nv = pair ? std::min(8, g.N) : kron_nv(g, true);
     ga.per_chain = g.nc + 1;
     ga.c = g.lam;
     ga.ec = std::exp(g.lam);
@@ -965,10 +968,10 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     ga.bins = g.bins;
     ga.kind = kB; ga.vec_is_col = 1; ga.bin_slot = 0;
     DQ_CLASS(ctx, kTGtauProp);
-    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A1, batch, ga, g.st));
+    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A1, batch, ga, pair, g.st));
     ga.kind = kBIT; ga.vec_is_col = 0; ga.bin_slot = 1;
     DQ_CLASS(ctx, kTGtauProp);
-    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, g.st));
+    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, pair, g.st));
     const size_t cnt = static_cast<size_t>(g.C) * (g.L + 1) * g.N;
     if (out_on_device) {
       DQ_CLASS(ctx, kTGtauFinal);

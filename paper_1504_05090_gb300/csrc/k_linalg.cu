@@ -397,6 +397,13 @@ template <typename T>
 __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N, const T* tx,
                                  const T* ty, const T* pre, const T* post);
 
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(df32 x) { return static_cast<double>(x); }
+
+// T = double, or df32 (float pairs) for groups whose working precision is
+// df32: the propagation between stabilisation points then runs on the FP32
+// pipe; the loaded G(c,0) / Y and the bins stay FP64.
+template <typename T>
 __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a) {
   const int b = blockIdx.y;
   const int chain = b / a.per_chain, blk = b - chain * a.per_chain;
@@ -405,39 +412,39 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
   const int nrows = min(nv, N - r0);
   const int lo = a.cp[blk], hi = a.cp[blk + 1];
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  double* v = reinterpret_cast<double*>(sm_raw);
-  double* tmp = v + nv * ld;
-  double* tx = tmp + nv * ld;
-  double* ty = tx + kMaxSide;
-  double* sc = ty + kMaxSide;
-  double* sbin = sc + N;
+  double* sbin = reinterpret_cast<double*>(sm_raw);
+  T* v = reinterpret_cast<T*>(sbin + N);
+  T* tmp = v + nv * ld;
+  T* tx = tmp + nv * ld;
+  T* ty = tx + kMaxSide;
+  T* sc = ty + kMaxSide;
   const bool inv = (a.kind == kBIT);
   if (threadIdx.x < kMaxSide) {
-    tx[threadIdx.x] = inv ? a.taps.exi[threadIdx.x] : a.taps.ex[threadIdx.x];
-    ty[threadIdx.x] = inv ? a.taps.eyi[threadIdx.x] : a.taps.ey[threadIdx.x];
+    tx[threadIdx.x] = static_cast<T>(inv ? a.taps.exi[threadIdx.x] : a.taps.ex[threadIdx.x]);
+    ty[threadIdx.x] = static_cast<T>(inv ? a.taps.eyi[threadIdx.x] : a.taps.ey[threadIdx.x]);
   }
   double* X = Xall + static_cast<size_t>(b) * a.mat_stride;
   for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
     const int vi = e / N, i = e - vi * N;
-    v[vi * ld + i] = X[static_cast<size_t>(r0 + vi) * N + i];
+    v[vi * ld + i] = static_cast<T>(X[static_cast<size_t>(r0 + vi) * N + i]);
   }
   for (int i = threadIdx.x; i < N; i += blockDim.x) sbin[i] = 0.0;
   const Geom g{a.Lx, a.Ly, N};
   const int8_t* f = a.field + static_cast<size_t>(chain) * a.L * N;
-  const double up = inv ? a.emc : a.ec, dn = inv ? a.ec : a.emc;
+  const T up = static_cast<T>(inv ? a.emc : a.ec), dn = static_cast<T>(inv ? a.ec : a.emc);
   for (int l = lo; l < hi; ++l) {
     __syncthreads();
     if (l > lo) {
       for (int i = threadIdx.x; i < N; i += blockDim.x)
         sc[i] = f[static_cast<size_t>(l - 1) * N + i] > 0 ? up : dn;
       __syncthreads();
-      kron_transform_d<double>(v, tmp, nrows, ld, a.Lx, a.Ly, N, tx, ty, sc, nullptr);
+      kron_transform_d<T>(v, tmp, nrows, ld, a.Lx, a.Ly, N, tx, ty, sc, nullptr);
     }
     for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
       const int vi = e / N, el = e - vi * N;
       const int q = r0 + vi;
       const int sep = a.vec_is_col ? sep_index(el, q, g) : sep_index(q, el, g);
-      atomicAdd(&sbin[sep], v[vi * ld + el]);
+      atomicAdd(&sbin[sep], to_d(v[vi * ld + el]));
     }
     __syncthreads();
     double* out = a.bins + ((static_cast<size_t>(chain) * (a.L + 1) + l) * 2 + a.bin_slot) * N;
@@ -463,26 +470,26 @@ __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, i
     const int vi = e / N, i = e - vi * N;
     const int x = i % Lx, y = i / Lx;
     const T* row = v + vi * ld + Lx * y;
-    T acc = T(0);
+    ProdSum<T> acc;
     for (int xp = 0; xp < Lx; ++xp) {
       int dd = x - xp;
       dd += dd < 0 ? Lx : 0;
-      acc = fma(tx[dd], row[xp], acc);
+      acc.add(tx[dd], row[xp]);
     }
-    tmp[vi * ld + i] = acc;
+    tmp[vi * ld + i] = acc.get();
   }
   __syncthreads();
   for (int e = threadIdx.x; e < tot; e += blockDim.x) {
     const int vi = e / N, i = e - vi * N;
     const int x = i % Lx, y = i / Lx;
     const T* col = tmp + vi * ld + x;
-    T acc = T(0);
+    ProdSum<T> acc;
     for (int yp = 0; yp < Ly; ++yp) {
       int dd = y - yp;
       dd += dd < 0 ? Ly : 0;
-      acc = fma(ty[dd], col[Lx * yp], acc);
+      acc.add(ty[dd], col[Lx * yp]);
     }
-    v[vi * ld + i] = post ? acc * post[i] : acc;
+    v[vi * ld + i] = post ? acc.get() * post[i] : acc.get();
   }
   __syncthreads();
 }
@@ -589,14 +596,21 @@ template cudaError_t launch_convert<double>(const double*, double*, long long, c
 template cudaError_t launch_convert<float>(const double*, float*, long long, cudaStream_t);
 template cudaError_t launch_convert<df32>(const double*, df32*, long long, cudaStream_t);
 
-cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, cudaStream_t st) {
-  const size_t sm = (2ull * a.nv * (a.N + 1) + 2 * kMaxSide + 2ull * a.N) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_gtau_propagate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(sm));
+template <typename T>
+static cudaError_t gtau_launch(double* X, int batch, const GtauArgs& a, cudaStream_t st) {
+  const size_t sm = a.N * sizeof(double) +
+                    (2ull * a.nv * (a.N + 1) + 2 * kMaxSide + static_cast<size_t>(a.N)) * sizeof(T);
+  cudaError_t e = cudaFuncSetAttribute(k_gtau_propagate<T>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
   if (e != cudaSuccess) return e;
   dim3 grid((a.N + a.nv - 1) / a.nv, batch);
-  k_gtau_propagate<<<grid, 256, sm, st>>>(X, a);
+  k_gtau_propagate<T><<<grid, 256, sm, st>>>(X, a);
   return cudaGetLastError();
+}
+
+cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, bool pair,
+                                  cudaStream_t st) {
+  return pair ? gtau_launch<df32>(X, batch, a, st) : gtau_launch<double>(X, batch, a, st);
 }
 
 cudaError_t launch_gtau_finalize(const double* bins, double* out, int C, int L, int Lx, int Ly,

@@ -54,34 +54,6 @@ __device__ __forceinline__ float shfl0(float x) { return __shfl_sync(0xFFFFFFFFu
 __device__ __forceinline__ double shfl0(double x) { return __shfl_sync(0xFFFFFFFFu, x, 0); }
 __device__ __forceinline__ df32 shfl0(df32 x) { return df32(shfl0(x.hi), shfl0(x.lo)); }
 
-// Sum of products s = sum_m u_m v_m.  For df32 the products are accumulated
-// with one TwoSum per term into (hi, lo) and rounded once at the end (about
-// 12 FP32 instructions per term instead of 27 for an exact df32 multiply-add;
-// relative error ~ m 2^-48).
-template <typename T>
-struct ProdSum {
-  T s;
-  __device__ __forceinline__ ProdSum() : s(T(0)) {}
-  __device__ __forceinline__ void add(T u, T v) { s = madd(u, v, s); }
-  __device__ __forceinline__ T get() const { return s; }
-};
-template <>
-struct ProdSum<df32> {
-  float hi, lo;
-  __device__ __forceinline__ ProdSum() : hi(0.0f), lo(0.0f) {}
-  __device__ __forceinline__ void add(df32 u, df32 v) {
-    const float p = u.hi * v.hi;
-    float e = fmaf(u.hi, v.hi, -p);
-    e = fmaf(u.hi, v.lo, e);
-    e = fmaf(u.lo, v.hi, e);
-    const float t = hi + p;
-    const float bb = t - hi;
-    lo += ((hi - (t - bb)) + (p - bb)) + e;
-    hi = t;
-  }
-  __device__ __forceinline__ df32 get() const { return df_fast_two_sum(hi, lo); }
-};
-
 // Sherman-Morrison coefficient -Delta_up / R_up in the working precision:
 // FP32 for float, FP64 for double, and a float reciprocal refined by one
 // Newton step in df32 arithmetic for df32 (no FP64 instruction).

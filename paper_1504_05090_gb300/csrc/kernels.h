@@ -128,7 +128,9 @@ struct GtauArgs {
   double* bins;          // [chain][L+1][2][N]
   int bin_slot;          // 0 for G(l,0), 1 for Y
 };
-cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, cudaStream_t st);
+// pair: propagate in float pairs (groups whose working precision is df32).
+cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, bool pair,
+                                  cudaStream_t st);
 // out[chain][l][k] from the bins (spin average, momentum transform).
 cudaError_t launch_gtau_finalize(const double* bins, double* out, int C, int L, int Lx, int Ly,
                                  cudaStream_t st);

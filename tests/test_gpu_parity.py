@@ -239,6 +239,20 @@ def test_gtau_matches_oracle(Lx, Ly, beta, dtau, ns):
             np.testing.assert_allclose(gt[c], ref, atol=1e-10 * np.max(np.abs(ref)))
 
 
+def test_gtau_float_pair_propagation_matches_fp64():
+    """Groups with float-pair working precision propagate G(l,0) and Y between
+    stabilisation points in float pairs; on the same fields the spin-averaged
+    G_k(tau) agrees with the FP64 propagation to 1e-9 of its maximum (the
+    stabilised G(c,0), Y and the bins are FP64 in both)."""
+    def groups(prec):
+        return [_grp(16, 16, U=2.0, beta=4.0, dtau=0.125, ns=8, C=2, prec=prec),
+                _grp(8, 8, U=3.0, beta=8.0, dtau=0.1, ns=10, C=2, prec=prec),
+                _grp(12, 6, U=2.0, beta=2.0, dtau=0.125, ns=4, C=1, prec=prec)]
+    with _sim(groups("df32"), seed=12) as a, _sim(groups("fp64"), seed=12) as b:
+        for x, y in zip(a.gtau(), b.gtau()):
+            np.testing.assert_allclose(x, y, rtol=0, atol=1e-9 * np.max(np.abs(y)))
+
+
 def test_gtau_on_device_equals_host():
     import torch
     g = _grp(4, 4, C=3)
