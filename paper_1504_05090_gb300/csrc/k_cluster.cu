@@ -509,6 +509,19 @@ cudaError_t launch_qrp_cluster(double* Xt, long long sX, double* Qt, long long s
 
 cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long sI, int n, int batch,
                               double* logabs, int* status, cudaStream_t st) {
+  // Small batches (the per-point recompute: one matrix per chain) spread each
+  // matrix over 4 CTAs, two of which fit on an SM (512 threads x 64
+  // registers), so that twice as many warps hide the step latency; large
+  // batches keep 2 CTAs per matrix.
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      nsm = 1;
+  }
+  if (4LL * batch <= 2LL * nsm)
+    return launch_cluster(k_gj_cluster<4>, 4, batch, st, A, sA, Ainv, sI, n, logabs, status);
   return launch_cluster(k_gj_cluster<2>, 2, batch, st, A, sA, Ainv, sI, n, logabs, status);
 }
 
