@@ -253,22 +253,25 @@ KronArgs kron_base(const Group& g, int kind, int nv) {
 }
 
 int kron_nv(const Group& g, bool fp64) {
-  // vectors per CTA: as many as fit comfortably in shared memory
+  // Vectors per CTA of the FP64 Kronecker transforms (stack products, G(tau)
+  // of FP64 groups, gradient): small tiles, so that several CTAs share an SM
+  // and their independent FMA chains keep the FP64 pipe busy (measured on the
+  // 16x16 sweep: 4 vectors 73 ms, 8 vectors 75 ms, 29 vectors 87 ms for the
+  // stack products).
   const int budget = fp64 ? 120 * 1024 : 110 * 1024;
   const int per = (g.N + 1) * 2 * (fp64 ? 8 : 4);
-  int nv = std::max(1, std::min(32, budget / per));
+  int nv = std::max(1, std::min(4, budget / per));
   return std::min(nv, g.N);
 }
 
-// Vectors per CTA of the slice wrap in the working precision.  The FP64
-// transforms are bound by the FP64 pipe and take large tiles; the float-pair
-// and FP32 ones run serial chains of compensated sums per element and need
-// many resident warps to hide their latency, hence small tiles (8 vectors,
-// about 35 KB of shared memory at N = 256: six CTAs per SM).
+// Vectors per CTA of the slice wrap in the working precision.  The
+// float-pair and FP32 transforms run serial chains of compensated sums per
+// element and need many resident warps to hide their latency: small tiles
+// (4 vectors, about 17 KB of shared memory at N = 256).
 template <typename T>
 int wrap_nv(const Group& g) {
   if (sizeof(T) == 8 && !std::is_same<T, df32>::value) return kron_nv(g, true);
-  return std::min(8, g.N);
+  return std::min(4, g.N);
 }
 
 GemmArgs gemm0(int n) {
