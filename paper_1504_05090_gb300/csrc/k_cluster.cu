@@ -377,10 +377,10 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
   __shared__ unsigned char used[kMaxN];
   __shared__ AM cand[2][CS];  // best unused owned row of every CTA for the next column
   __shared__ double sinv;
+  __shared__ double pivs[kMaxN];  // |pivot| of every step (log|det A| after the loop)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
   int pend_row = -1;  // owned pivot row whose scaled values wait in pend[]
-  double la = 0.0;
   __syncthreads();
   // warp 0: best |A[i][col]| over the owned unused rows, sent to every CTA
   auto publish = [&](int col, int slot) {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
         atomicExch(status, kDevSingular);
         piv = DBL_MIN;
       }
-      la += log(absd(piv));
+      pivs[k] = absd(piv);
       sinv = 1.0 / piv;
     }
     __syncthreads();
@@ -480,7 +480,19 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
     for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
       Ainv[static_cast<size_t>(k) * n + jj] = Zr[ip[jj]];
   }
-  if (rank == 0 && threadIdx.x == 0 && logabs) logabs[b] = la;
+  if (logabs && rank == 0) {  // log|det| = sum_k log|pivot_k|, off the step loop
+    double la = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) la += log(pivs[k]);
+    la = wsum(la);
+    __shared__ double lsum[32];
+    if (lane == 0) lsum[w] = la;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int q = 0; q < nw; ++q) t += lsum[q];
+      logabs[b] = t;
+    }
+  }
 }
 
 template <typename K, typename... Args>
