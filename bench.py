@@ -329,9 +329,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "df32+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "df32 (float pairs) Metropolis/delayed "
-                       "update/wrap, fp64 UDV/QR stabilisation, G recompute, drift, G(tau)",
-                       "chains_per_gpu": W["chains"], "L2": "working set > L2 (no flush needed)"},
+            "config": bench_config(),
             "drift": mixed["drift"], "acceptance": mixed["acceptance"],
             "fp64_plain": {"value": world * updates_per_sweep(W["chains"]) / (ms64 / 1e3),
                            "ms_per_step": ms64, "drift": plain["drift"],
@@ -462,6 +460,13 @@ def run_config(args):
                               "acceptance": float(a.sum()) / (n_up * args.steps)}), flush=True)
 
 
+def bench_config():
+    """The workload description both arms report."""
+    return {"workload": WORKLOAD, "precision": "df32 (float pairs) Metropolis/delayed "
+            "update/wrap/G(tau) propagation, fp64 UDV/QR stabilisation, G recompute, drift",
+            "chains_per_gpu": W["chains"], "L2": "working set > L2 (no flush needed)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -481,10 +486,12 @@ def run_reference(args):
     sample = ("%d chains of the workload per step (one full oracle sweep incl. G(tau) per "
               "single-threaded process)" % workers)
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "oracle": "oracle/dqmc.py (numpy/scipy FP64)"},
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": bench_config(),
+        "reference": "the FP64 CPU oracle (oracle/dqmc.py) on the host cores: no reference "
+                     "implementation exists for this paper",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
