@@ -50,6 +50,31 @@ def updates_per_sweep(chains):
 
 
 # ---------------------------------------------------------------------------
+# Several GPUs (torchrun, one rank per GPU): replicas only.  Every rank runs
+# the whole workload with its own seed (independent Markov chains, no data
+# exchange); the step time is the maximum over ranks and the value counts the
+# updates of all ranks (weak scaling).
+# ---------------------------------------------------------------------------
+def rank_seed(rank):
+    return 1000 * rank
+
+
+def max_over_ranks(x, dist, device):
+    """Maximum of a float over the ranks of `dist` (None: one rank)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, ms_per_step):
+    """HS-field updates per second of the whole job."""
+    return world * updates_per_sweep(W["chains"]) / (ms_per_step / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle timing (host cores): one worker process per core, each sweeps
 # one chain of the workload once; started with `spawn` before any CUDA call.
 # ---------------------------------------------------------------------------
@@ -160,6 +185,8 @@ def time_arm(pkg, torch, precision, steps, warmup, seed, dist):
             step_device(sim, gbuf)
         e1.record(st)
         torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     ms = e0.elapsed_time(e1) / steps
     launches = sim.launch_count() - l0
     drift, acc = sim.stats()
@@ -277,7 +304,7 @@ def e2e_arm(pkg, torch, sim, steps):
         nbytes = sum(a.nbytes for a in gt) + ob.nbytes
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
-    return {"value": updates_per_sweep(W["chains"]) / dt, "unit": UNIT, "h2d_bytes_per_step": 0,
+    return {"ms": dt * 1e3, "unit": UNIT, "h2d_bytes_per_step": 0,
             "d2h_bytes_per_step": int(nbytes)}
 
 
@@ -295,7 +322,7 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    seed = 1000 * rank  # independent chains per rank (weak scaling)
+    seed = rank_seed(rank)  # independent chains per rank (weak scaling)
 
     # Mixed arm: float-pair (df32) Metropolis / delayed update / wrap on the FP32
     # pipe with FP64 stabilisation -- the same G drift as plain FP64 (see
@@ -314,16 +341,15 @@ def run_ours(args):
     plain = arms["fp64"]
 
     def slowest(ms):
-        if not dist:
-            return ms
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(ms, dist, "cuda")
 
     ms = slowest(mixed["ms"])
     roof, roof_rows = roofline(prof, args.steps, mixed["acceptance"], "df32")
     ms64 = slowest(plain["ms"])
-    value = world * updates_per_sweep(W["chains"]) / (ms / 1e3)
+    ms32 = slowest(arms["fp32"]["ms"])  # every rank joins every reduction
+    e2e_ms = slowest(e2e.pop("ms"))
+    e2e["value"] = job_value(world, e2e_ms)
+    value = job_value(world, ms)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -331,13 +357,12 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "df32+f64", "data": "synthetic",
             "config": bench_config(),
             "drift": mixed["drift"], "acceptance": mixed["acceptance"],
-            "fp64_plain": {"value": world * updates_per_sweep(W["chains"]) / (ms64 / 1e3),
+            "fp64_plain": {"value": job_value(world, ms64),
                            "ms_per_step": ms64, "drift": plain["drift"],
                            "speedup_mixed_over_fp64": ms64 / ms,
                            "kernel_ms_per_step": plain["kernel_ms_per_step"]},
-            "fp32_working": {"value": world * updates_per_sweep(W["chains"]) /
-                             (slowest(arms["fp32"]["ms"]) / 1e3),
-                             "ms_per_step": arms["fp32"]["ms"], "drift": arms["fp32"]["drift"],
+            "fp32_working": {"value": job_value(world, ms32),
+                             "ms_per_step": ms32, "drift": arms["fp32"]["drift"],
                              "kernel_ms_per_step": arms["fp32"]["kernel_ms_per_step"]},
             "roofline": roof,
             "roofline_by_class": roof_rows,
