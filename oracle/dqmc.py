@@ -51,6 +51,10 @@ points the paper leaves open:
   R8  G(tau_l) on l = 0..L with origin tau = 0; the momentum-resolved output
       is Re G_k(tau_l) = (1/N) sum_ij cos(k.(r_i - r_j)) G_ij(l, 0),
       averaged over the two spins.
+  R14 the real-space spin correlation of Sec. 4 (Fig. 5) is read as the
+      longitudinal C(r) = (1/N) sum_i <S^z_i S^z_{i+r}>, S^z = (n_up - n_dn)/2,
+      averaged over translations and accumulated at the R5 measurement points;
+      the paper names neither the component nor the normalisation.
 """
 from __future__ import annotations
 
@@ -65,7 +69,7 @@ __all__ = [
     "adjacency", "dispersion", "exp_hopping", "hs_lambda", "hs_prefactor",
     "n_slices", "b_matrix", "b_inverse", "udv_chain", "green_from_udv",
     "two_stack_green", "Params", "Chain", "observables_from_g",
-    "momentum_diag", "weight_log",
+    "spin_correlation_from_g", "momentum_diag", "weight_log",
 ]
 
 MASK32 = 0xFFFFFFFF
@@ -304,6 +308,34 @@ def observables_from_g(G_up, G_dn, K):
     return np.array([n, docc, ekin / N])
 
 
+def spin_correlation_from_g(G_up, G_dn, Lx, Ly):
+    """Real-space equal-time spin correlation of one configuration, averaged
+    over lattice translations (Sec. 4, Fig. 5; reading R14):
+      C(r) = (1/N) sum_i <S^z_i S^z_{i+r}>,   S^z_i = (n_i,up - n_i,dn) / 2,
+    r = (dx, dy) periodic, stored at index dx + Lx dy.  For a fixed Ising
+    field the two spins are independent one-body problems, so Wick's theorem
+    gives, with n_i,s = 1 - G_s,ii and <c^dag_i c_j> = delta_ij - G_s,ji,
+      <n_i,s n_j,s'> = n_i,s n_j,s' + delta_ss' (delta_ij - G_s,ji) G_s,ij.
+    Both spins are used as given (no particle-hole identity)."""
+    N = Lx * Ly
+    nu = 1.0 - np.diag(G_up)
+    nd = 1.0 - np.diag(G_dn)
+    x = np.arange(N) % Lx
+    y = np.arange(N) // Lx
+    i = np.arange(N)
+    C = np.zeros(N)
+    for dy in range(Ly):
+        for dx in range(Lx):
+            j = site_index((x + dx) % Lx, (y + dy) % Ly, Lx)
+            d = (i == j).astype(np.float64)
+            uu = nu[i] * nu[j] + (d - G_up[j, i]) * G_up[i, j]
+            dd = nd[i] * nd[j] + (d - G_dn[j, i]) * G_dn[i, j]
+            ud = nu[i] * nd[j]
+            du = nd[i] * nu[j]
+            C[site_index(dx, dy, Lx)] = np.sum(0.25 * (uu + dd - ud - du)) / N
+    return C
+
+
 def momentum_diag(X, Lx, Ly):
     """Re X_k = (1/N) sum_ij cos(k.(r_i - r_j)) X_ij for all k (index kx + Lx ky).
     Written as the sum over separations r = r_i - r_j first, then cosines."""
@@ -410,6 +442,7 @@ class Chain:
         accepted = 0
         drift = 0.0
         obs = []
+        spin = []
         ratios = []
         for l in range(1, L + 1):
             u = proposal_uniforms(self.seed, self.chain, w, l - 1, N)
@@ -435,8 +468,9 @@ class Chain:
                     G[sg] = Gf
                 if measure:
                     obs.append(observables_from_g(G[1], G[-1], p.K))
+                    spin.append(spin_correlation_from_g(G[1], G[-1], p.Lx, p.Ly))
         self.sweeps_done += 1
-        return {"accepted": accepted, "drift": drift, "obs": obs,
+        return {"accepted": accepted, "drift": drift, "obs": obs, "spin": spin,
                 "ratios": np.array(ratios), "G_up": G[1], "G_dn": G[-1]}
 
     # -- unequal-time Green function (Sec. 2: G_ij(tau_l) on the slice grid) --

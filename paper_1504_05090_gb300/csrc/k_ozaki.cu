@@ -124,9 +124,12 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
   const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (v >= nrt * R) return;
   __nv_bfloat16* out = outall + b * sOut;
+  // Each lane owns 8 consecutive K elements: they are adjacent in the core-matrix
+  // layout (np is a multiple of 32), so each digit slice takes one 16-byte store.
   if (v >= n) {  // padding rows of the last row tile
-    for (int k = lane; k < np; k += 32)
-      for (int p = 0; p < kS; ++p) out[oz_offset(p, v, k, R, nrt, nkc)] = __float2bfloat16_rn(0.0f);
+    for (int k0 = lane * 8; k0 < np; k0 += 256)
+      for (int p = 0; p < kS; ++p)
+        *reinterpret_cast<uint4*>(out + oz_offset(p, v, k0, R, nrt, nkc)) = make_uint4(0, 0, 0, 0);
     return;
   }
   int emax = -100000;
@@ -137,26 +140,45 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
   }
   for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
   if (lane == 0) exall[b * sEx + v] = emax - 6;
-  for (int k = lane; k < np; k += 32) {
-    unsigned long long al = 0;
-    float sg = 1.0f;
-    if (k < n) {
-      const double x = (ks_mode != 0) ? M[v * sv + k * sk] * ksv[k] : M[v * sv + k * sk];
-      const long long bits = __double_as_longlong(x);
-      const int E = static_cast<int>((bits >> 52) & 0x7FF);
-      if (E != 0) {  // zero and subnormal inputs contribute zero digits
-        const unsigned long long mant =
-            (static_cast<unsigned long long>(bits) & ((1ULL << 52) - 1)) | (1ULL << 52);
-        const int sh = emax - (E - 1023 + kev[k]);
-        al = (sh < 64) ? (mant >> sh) : 0ULL;
+  for (int k0 = lane * 8; k0 < np; k0 += 256) {
+    unsigned long long al[8];
+    float sg[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      al[e] = 0;
+      sg[e] = 1.0f;
+      if (k < n) {
+        const double x = (ks_mode != 0) ? M[v * sv + k * sk] * ksv[k] : M[v * sv + k * sk];
+        const long long bits = __double_as_longlong(x);
+        const int E = static_cast<int>((bits >> 52) & 0x7FF);
+        if (E != 0) {  // zero and subnormal inputs contribute zero digits
+          const unsigned long long mant =
+              (static_cast<unsigned long long>(bits) & ((1ULL << 52) - 1)) | (1ULL << 52);
+          const int sh = emax - (E - 1023 + kev[k]);
+          al[e] = (sh < 64) ? (mant >> sh) : 0ULL;
+        }
+        sg[e] = (bits < 0) ? -1.0f : 1.0f;
       }
-      sg = (bits < 0) ? -1.0f : 1.0f;
     }
 #pragma unroll
     for (int p = 0; p < kS; ++p) {
-      const int a = (p < 7) ? static_cast<int>((al >> (46 - 7 * p)) & 127ULL)
-                            : static_cast<int>((al & 15ULL) << 3);
-      out[oz_offset(p, v, k, R, nrt, nkc)] = __float2bfloat16_rn(sg * static_cast<float>(a));
+      uint32_t w[4];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        float f[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const unsigned long long a = al[e + q];
+          const int d = (p < 7) ? static_cast<int>((a >> (46 - 7 * p)) & 127ULL)
+                                : static_cast<int>((a & 15ULL) << 3);
+          f[q] = sg[e + q] * static_cast<float>(d);
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(f[0], f[1]);  // .x = f[0], low half
+        w[e >> 1] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      *reinterpret_cast<uint4*>(out + oz_offset(p, v, k0, R, nrt, nkc)) =
+          make_uint4(w[0], w[1], w[2], w[3]);
     }
   }
 }

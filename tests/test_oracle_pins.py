@@ -153,6 +153,68 @@ def test_equal_time_observables_enumeration_vs_fock(tiny):
     assert mean[2] == pytest.approx(F.ekin(), rel=1e-11)
 
 
+def _fock_szsz_by_displacement(nu, nd, Lx, Ly):
+    """Diagonal of (1/N) sum_i S^z_i S^z_{i+r} in the occupation basis, one
+    row per displacement r = dx + Lx dy, from the occupation arrays alone."""
+    N = Lx * Ly
+    m = 0.5 * (nu - nd)
+    out = np.empty((N, nu.shape[0]))
+    for dy in range(Ly):
+        for dx in range(Lx):
+            shift = [((i % Lx + dx) % Lx) + Lx * ((i // Lx + dy) % Ly) for i in range(N)]
+            out[dx + Lx * dy] = np.sum(m * m[:, shift], axis=1) / N
+    return out
+
+
+def test_spin_correlation_enumeration_vs_fock(tiny):
+    """Weighted field average of the oracle's C(r) == Tr[T^L S^z_i S^z_{i+r}]/Z
+    of the interacting model, for every displacement of the 2x2 cluster."""
+    p, fields, w, greens, F = tiny
+    C = np.array([o.spin_correlation_from_g(greens[1][f], greens[-1][f], p.Lx, p.Ly)
+                  for f in range(len(w))])
+    mean = (w[:, None] * C).sum(0) / w.sum()
+    ops = _fock_szsz_by_displacement(F.nu, F.nd, p.Lx, p.Ly)
+    exact = np.array([F.expect(np.diag(op)) for op in ops])
+    np.testing.assert_allclose(mean, exact, rtol=1e-11, atol=1e-14)
+    assert exact[0] > 0.0 and exact[p.Lx + 0] < 0.0  # local moment; nearest neighbours anti-aligned
+
+
+def test_spin_correlation_single_field_vs_fock():
+    """For ONE Ising field the fermions are free: C(r) from the oracle's Wick
+    contraction equals the Fock-space trace Tr[P O_r]/Tr[P] with
+    P = prod_l (e^{-dtau h} x e^{-dtau h}) e^{lambda s_l (n_up - n_dn)},
+    built from the occupation basis, for random fields of a 3x2 cluster.
+    Tr P = det(I + A_up) det(I + A_dn) pins the Fock product itself."""
+    Lx, Ly, L = 3, 2, 3
+    p = o.Params(Lx, Ly, 0.25, 3.0, L * 0.2, 0.2, n_s=1)
+    N = p.N
+    occ = fock.occupations(N)
+    eh = fock._expm_sym(fock.single_spin_hopping(Lx, Ly, p.t), -p.dtau)
+    ops = _fock_szsz_by_displacement(
+        np.tile(occ, (1 << N, 1)), np.repeat(occ, 1 << N, axis=0), Lx, Ly)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        s = rng.choice([-1, 1], size=(L, N)).astype(np.int8)
+        P = np.eye(1 << (2 * N))
+        for l in range(L):
+            hu = np.exp(p.lam * (occ @ s[l].astype(np.float64)))   # up:  e^{+lambda s.n}
+            hd = np.exp(-p.lam * (occ @ s[l].astype(np.float64)))  # down: e^{-lambda s.n}
+            T = np.kron(eh * hd[None, :], eh * hu[None, :])          # down slow, up fast
+            P = T @ P
+        trP = np.trace(P)
+        G, det = {}, {}
+        for sg in (1, -1):
+            A = np.eye(N)
+            for l in range(L):
+                A = o.b_matrix(p.E, p.lam, sg, s[l]) @ A
+            det[sg] = np.linalg.det(np.eye(N) + A)
+            G[sg] = np.linalg.inv(np.eye(N) + A)
+        assert trP == pytest.approx(det[1] * det[-1], rel=1e-10)
+        exact = np.array([np.sum(np.diag(P) * op) for op in ops]) / trP
+        got = o.spin_correlation_from_g(G[1], G[-1], Lx, Ly)
+        np.testing.assert_allclose(got, exact, rtol=1e-9, atol=1e-12)
+
+
 @pytest.mark.parametrize("l", [0, 1, 2, 3])
 def test_unequal_time_green_enumeration_vs_fock(tiny, l):
     """Weighted field average of the oracle's G(l,0) == Tr[T^{L-l} c_i T^l c_j^dag]/Z."""
