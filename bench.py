@@ -293,7 +293,8 @@ def roofline(profile, steps, acceptance, precision="df32"):
 
 def e2e_arm(pkg, torch, sim, steps):
     """Same metric through the public API with host outputs: every step copies
-    G(k, tau) of all chains and the observables to host memory."""
+    G(k, tau) of all chains, the observables and the spin correlation to host
+    memory."""
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     nbytes = 0
@@ -301,7 +302,8 @@ def e2e_arm(pkg, torch, sim, steps):
         sim.sweep(1, measure=True)
         gt = sim.gtau()
         ob = sim.observables()
-        nbytes = sum(a.nbytes for a in gt) + ob.nbytes
+        sc = sim.spin_correlation()
+        nbytes = sum(a.nbytes for a in gt) + ob.nbytes + sum(a.nbytes for a in sc)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
     return {"ms": dt * 1e3, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -173,6 +173,19 @@ int dqmc_get_G(const dqmc_ctx* ctx, int chain, int spin, double* out);
 int dqmc_get_observables(const dqmc_ctx* ctx, double* out);
 int dqmc_reset_observables(dqmc_ctx* ctx);
 
+/* Accumulated real-space spin correlation of Sec. 4 (Fig. 5), measured at the
+ * same points as the observables above and zeroed with them by
+ * dqmc_reset_observables:
+ *   C(r) = (1/N) sum_i <S^z_i S^z_{i+r}>,  S^z_i = (n_i,up - n_i,dn) / 2,
+ * r = (dx, dy) periodic, from Wick's theorem on the stabilised FP64 G_up and
+ * G_dn = I - P G_up^T P of each configuration.  out: host doubles, for each
+ * group in creation order [chain][N_g] with element dx + Lx dy, summed over
+ * the measurements (divide by the count in the observables' last column);
+ * dqmc_spin_correlation_size gives the total count of doubles (-1 for a null
+ * context).  DQMC_ERR_ARG for null pointers; DQMC_ERR_CUDA if the copy fails. */
+int64_t dqmc_spin_correlation_size(const dqmc_ctx* ctx);
+int dqmc_get_spin_correlation(const dqmc_ctx* ctx, double* out);
+
 /* Per-chain statistics since the last reset: maximum G drift seen at a
  * stabilisation point (host doubles [chain]) and accepted flips (host
  * uint64 [chain]); either pointer may be NULL. */

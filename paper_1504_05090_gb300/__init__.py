@@ -136,6 +136,14 @@ class DQMC:
         _lib.check(lib().dqmc_get_observables(self._h, _ptr(out)), "dqmc_get_observables", lib())
         return out
 
+    def spin_correlation(self):
+        """Accumulated C(r) per group, arrays [chain, N] with r = dx + Lx dy
+        (sums over the measurements; reset with reset_observables)."""
+        out = np.empty(lib().dqmc_spin_correlation_size(self._h))
+        _lib.check(lib().dqmc_get_spin_correlation(self._h, _ptr(out)),
+                   "dqmc_get_spin_correlation", lib())
+        return self._split(out, lambda g: (g.n_chains, g.N))
+
     def reset_observables(self):
         _lib.check(lib().dqmc_reset_observables(self._h), "dqmc_reset_observables", lib())
 

@@ -78,6 +78,7 @@ struct Group {
   double *X = nullptr, *Rtil = nullptr;
   double *Mid = nullptr, *W1 = nullptr, *W2 = nullptr, *A1 = nullptr, *A2 = nullptr;
   double *logabs = nullptr, *obs = nullptr, *drift = nullptr, *bins = nullptr, *gacc = nullptr;
+  double* spin = nullptr;  // [C][N] accumulated spin correlation C(r)
   double* gout = nullptr;  // [C][L+1][N] staging of G(tau) for host output
   double* qrs = nullptr;   // [C][2N] column norms of the QR
   void* oz = nullptr;      // digit slices of the tensor-core FP64 GEMM
@@ -503,7 +504,8 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
       DQ_RET(recompute(ctx, g, j));
       DQ_RET(drift_reset<T>(ctx, g));
       if (measure)
-        DQ_LAUNCH_C(ctx, kTMisc, launch_observables(g.G64, g.C, g.p.Lx, g.p.Ly, g.p.t, g.obs, g.st));
+        DQ_LAUNCH_C(ctx, kTMisc, launch_observables(g.G64, g.C, g.p.Lx, g.p.Ly, g.p.t, g.obs, g.spin,
+                                                       g.st));
       ++j;
     }
   }
@@ -653,6 +655,7 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
   DQ_RET(dev_alloc(ctx, &g.A2, C * S * NN * 8));
   DQ_RET(dev_alloc(ctx, &g.logabs, C * S * 8));
   DQ_RET(dev_alloc(ctx, &g.obs, C * 4 * 8));
+  DQ_RET(dev_alloc(ctx, &g.spin, C * N * 8));
   DQ_RET(dev_alloc(ctx, &g.drift, C * 8));
   DQ_RET(dev_alloc(ctx, &g.acc, C * 8));
   DQ_RET(dev_alloc(ctx, &g.bins, C * (g.L + 1) * 2 * N * 8));
@@ -673,6 +676,7 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
   DQ_CK(cudaMemcpyAsync(g.d_cp_grad, cpd.data(), cpd.size() * sizeof(int), cudaMemcpyHostToDevice,
                         ctx->st));
   DQ_CK(cudaMemsetAsync(g.obs, 0, C * 4 * 8, ctx->st));
+  DQ_CK(cudaMemsetAsync(g.spin, 0, C * N * 8, ctx->st));
   DQ_CK(cudaMemsetAsync(g.drift, 0, C * 8, ctx->st));
   DQ_CK(cudaMemsetAsync(g.acc, 0, C * 8, ctx->st));
   return DQMC_OK;
@@ -1116,7 +1120,29 @@ int dqmc_get_observables(const dqmc_ctx* ctx, double* out) {
 
 int dqmc_reset_observables(dqmc_ctx* ctx) {
   if (!ctx) return DQMC_ERR_ARG;
-  for (Group& g : ctx->g) DQ_CK(cudaMemsetAsync(g.obs, 0, g.C * 4 * sizeof(double), ctx->st));
+  for (Group& g : ctx->g) {
+    DQ_CK(cudaMemsetAsync(g.obs, 0, g.C * 4 * sizeof(double), ctx->st));
+    DQ_CK(cudaMemsetAsync(g.spin, 0, static_cast<size_t>(g.C) * g.N * sizeof(double), ctx->st));
+  }
+  return DQMC_OK;
+}
+
+int64_t dqmc_spin_correlation_size(const dqmc_ctx* ctx) {
+  if (!ctx) return -1;
+  int64_t n = 0;
+  for (const Group& g : ctx->g) n += static_cast<int64_t>(g.C) * g.N;
+  return n;
+}
+
+int dqmc_get_spin_correlation(const dqmc_ctx* ctx, double* out) {
+  if (!ctx || !out) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (const Group& g : ctx->g) {
+    const size_t n = static_cast<size_t>(g.C) * g.N;
+    DQ_CK(cudaMemcpyAsync(out + off, g.spin, n * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+    off += n;
+  }
+  DQ_CK(cudaStreamSynchronize(ctx->st));
   return DQMC_OK;
 }
 

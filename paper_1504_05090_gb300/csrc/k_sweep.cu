@@ -611,13 +611,43 @@ __global__ void __launch_bounds__(256) k_drift_reset(const double* G64, T* Gw, i
 // Equal-time observables of one configuration from the stabilised G_up
 // (G_dn = I - P G_up^T P):  n = (1/N) sum_i [(1 - G_ii) + G_ii],
 // docc = (1/N) sum_i (1 - G_ii) G_ii,
-// ekin = (1/N) sum_sigma sum_ij K_ij <c^dag_i c_j> = (2t/N) sum_j sum_delta G_{j, j+delta}.
+// ekin = (1/N) sum_sigma sum_ij K_ij <c^dag_i c_j> = (2t/N) sum_j sum_delta G_{j, j+delta},
+// and the translation-averaged spin correlation of Sec. 4 (Fig. 5),
+// C(r) = (1/N) sum_i <S^z_i S^z_{i+r}>, S^z = (n_up - n_dn)/2, accumulated into
+// spin[c][r], r = dx + Lx dy.  Wick's theorem per spin with G_dn = I - P G_up^T P
+// gives, for a = G_ij, b = G_ji, d = delta_ij, p = p_i p_j = (-1)^(dx+dy) (even
+// sides) and m_i = n_i,up - n_i,dn = 1 - 2 G_ii:
+//   4 <S^z_i S^z_j> = m_i m_j + (d - b) a + p a (d - p b)
+// (spin-up exchange, then spin-down exchange).
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_observables(const double* G64, int Lx, int Ly, double t,
-                                                    double* obs) {
+                                                    double* obs, double* spin) {
   const int c = blockIdx.x;
   const int N = Lx * Ly;
   const double* G = G64 + static_cast<size_t>(c) * N * N;
+  __shared__ double m[kMaxN];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) m[i] = 1.0 - 2.0 * G[static_cast<size_t>(i) * N + i];
+  __syncthreads();
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    const int dx = r % Lx, dy = r / Lx;
+    const double p = ((dx + dy) & 1) ? -1.0 : 1.0;
+    double acc = 0.0;
+    int y = 0, yj = dy;
+    for (; y < Ly; ++y) {
+      const int row0 = Lx * y, rowj = Lx * yj;
+#pragma unroll 4
+      for (int x = 0; x < Lx; ++x) {
+        const int xj = (x + dx < Lx) ? x + dx : x + dx - Lx;
+        const int i = row0 + x, j = rowj + xj;
+        const double a = G[static_cast<size_t>(i) * N + j];
+        const double b = G[static_cast<size_t>(j) * N + i];
+        const double d = (i == j) ? 1.0 : 0.0;
+        acc += m[i] * m[j] + (d - b) * a + p * a * (d - p * b);
+      }
+      yj = (yj + 1 == Ly) ? 0 : yj + 1;
+    }
+    spin[static_cast<size_t>(c) * N + r] += acc / (4.0 * N);
+  }
   double n = 0.0, dc = 0.0, ek = 0.0;
   for (int j = threadIdx.x; j < N; j += blockDim.x) {
     const double g = G[static_cast<size_t>(j) * N + j];
@@ -735,8 +765,8 @@ cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* d
 }
 
 cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
-                               cudaStream_t st) {
-  k_observables<<<C, 256, 0, st>>>(G64, Lx, Ly, t, obs);
+                               double* spin, cudaStream_t st) {
+  k_observables<<<C, 256, 0, st>>>(G64, Lx, Ly, t, obs, spin);
   return cudaGetLastError();
 }
 

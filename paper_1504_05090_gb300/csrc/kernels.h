@@ -84,7 +84,7 @@ template <typename T>
 cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* drift, int* status,
                                cudaStream_t st);
 cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
-                               cudaStream_t st);
+                               double* spin, cudaStream_t st);
 
 cudaError_t launch_gemm(const GemmArgs& a, int batch, cudaStream_t st);
 // The same product on the tcgen05 tensor cores with FP64-level accuracy

@@ -72,6 +72,7 @@ def test_sweeps_match_oracle(Lx, Ly, beta, dtau, ns, k, C):
     with _sim([g], seed=11) as sim:
         chains = [o.Chain(p, seed=11, chain=c) for c in range(C)]
         ref_obs = np.zeros((C, 4))
+        ref_spin = np.zeros((C, g.N))
         ref_acc = np.zeros(C)
         for sweep in range(2):
             sim.sweep(1, measure=True)
@@ -79,6 +80,7 @@ def test_sweeps_match_oracle(Lx, Ly, beta, dtau, ns, k, C):
                 out = ch.sweep()
                 ref_acc[c] += out["accepted"]
                 ref_obs[c, :3] += np.sum(out["obs"], axis=0)
+                ref_spin[c] += np.sum(out["spin"], axis=0)
                 ref_obs[c, 3] += len(out["obs"])
                 assert np.array_equal(sim.field()[0][c], ch.field), (sweep, c)
                 assert _rel(sim.G(c, 0), out["G_up"]) < GTOL
@@ -89,6 +91,7 @@ def test_sweeps_match_oracle(Lx, Ly, beta, dtau, ns, k, C):
         obs = sim.observables()
         np.testing.assert_array_equal(obs[:, 3], ref_obs[:, 3])
         np.testing.assert_allclose(obs[:, :3], ref_obs[:, :3], rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(sim.spin_correlation()[0], ref_spin, rtol=1e-9, atol=1e-12)
 
 
 def test_two_groups_in_one_context_match_oracle():
@@ -118,6 +121,8 @@ def test_graph_replay_equals_direct_launches():
         for c in range(5):
             assert np.array_equal(a.G(c, 0), b.G(c, 0))
         np.testing.assert_array_equal(a.observables(), b.observables())
+        for sa, sb in zip(a.spin_correlation(), b.spin_correlation()):
+            np.testing.assert_array_equal(sa, sb)
 
 
 def test_concurrent_group_branches_equal_serial_launches():
@@ -189,6 +194,8 @@ def test_metropolis_split_over_a_cluster_is_invisible(prec):
                 assert np.array_equal(sim.G(c, 0), ref.G(c, 0))
             assert np.array_equal(sim.stats()[1], ref.stats()[1])
             np.testing.assert_array_equal(sim.observables(), ref.observables())
+            for sa, sb in zip(sim.spin_correlation(), ref.spin_correlation()):
+                np.testing.assert_array_equal(sa, sb)
     finally:
         for sim in sims:
             sim.close()
@@ -411,3 +418,12 @@ def test_full_size_16x16_sampled_chains():
         drift, acc = sim.stats()
         assert acc[0] == out["accepted"]
         assert np.all(drift < 1e-8)
+        # spin correlation: chain 0 element by element against the oracle; every
+        # chain through properties that hold at any size
+        spin, obs = sim.spin_correlation()[0], sim.observables()
+        np.testing.assert_allclose(spin[0], np.sum(out["spin"], axis=0), rtol=1e-9, atol=1e-12)
+        # C(r) = C(-r): S^z_i S^z_{i+r} summed over i is symmetric in r
+        minus = [((-dx) % 16) + 16 * ((-dy) % 16) for dy in range(16) for dx in range(16)]
+        np.testing.assert_allclose(spin[:, minus], spin, rtol=1e-12, atol=1e-14)
+        # C(0) = <(S^z)^2> = (n - 2 docc) / 4 per site, from the separate observables
+        np.testing.assert_allclose(spin[:, 0], (obs[:, 0] - 2.0 * obs[:, 1]) / 4.0, rtol=1e-12)
