@@ -55,12 +55,19 @@ points the paper leaves open:
       longitudinal C(r) = (1/N) sum_i <S^z_i S^z_{i+r}>, S^z = (n_up - n_dn)/2,
       averaged over translations and accumulated at the R5 measurement points;
       the paper names neither the component nor the normalisation.
+  R15 dtau -> 0 extrapolation of G_k(tau) (Sec. 3, Fig. 2): the alignment
+      spline is not given (its footnote is missing) and is read as the
+      not-a-knot cubic spline on each run's uniform grid; the pointwise
+      extrapolation is a least-squares fit in dtau^2, the order of the
+      Trotter error of the momentum-diagonal G_k(tau) (the K/V split is
+      similar to the symmetric one there).
 """
 from __future__ import annotations
 
 import math
 
 import numpy as np
+import scipy.interpolate
 import scipy.linalg
 
 __all__ = [
@@ -69,7 +76,7 @@ __all__ = [
     "adjacency", "dispersion", "exp_hopping", "hs_lambda", "hs_prefactor",
     "n_slices", "b_matrix", "b_inverse", "udv_chain", "green_from_udv",
     "two_stack_green", "Params", "Chain", "observables_from_g",
-    "spin_correlation_from_g", "momentum_diag", "weight_log",
+    "spin_correlation_from_g", "momentum_diag", "weight_log", "trotter_extrapolate",
 ]
 
 MASK32 = 0xFFFFFFFF
@@ -350,6 +357,33 @@ def momentum_diag(X, Lx, Ly):
                                  indexing="ij")
     phase = np.cos(2 * np.pi * (kx * rx / Lx + ky * ry / Ly))
     return (phase * g[None, None, :, :]).sum(axis=(2, 3)).reshape(-1) / N
+
+
+# ---------------------------------------------------------------------------
+# Trotter extrapolation of G_k(tau) (Sec. 3, Fig. 2; reading R15).
+# ---------------------------------------------------------------------------
+def trotter_extrapolate(dtaus, gks, beta, M):
+    """dtau -> 0 limit of G_k(tau) from runs at several time steps.
+    Run r has time step dtaus[r] and data gks[r] of shape [C_r, L_r + 1, N]
+    (G_k(tau_l) on its own grid tau_l = l dtau_r, per chain).  Steps, as the
+    paper orders them: average each run over its chains; put every run on
+    the common fine grid tau_m = m beta / M (m = 0..M) with a cubic spline
+    through its L_r + 1 points (not-a-knot ends); at every (tau_m, k) fit the
+    runs by least squares to a + b dtau^2 and keep a.  One run returns its
+    interpolation.  Returns [M + 1, N]."""
+    taus = np.arange(M + 1) * (beta / M)
+    vals = []
+    for dt, g in zip(dtaus, gks):
+        g = np.asarray(g, dtype=np.float64)
+        mean = g.mean(axis=0)
+        grid = np.arange(g.shape[1]) * dt
+        vals.append(scipy.interpolate.CubicSpline(grid, mean, axis=0, bc_type="not-a-knot")(taus))
+    vals = np.array(vals)
+    if len(vals) == 1:
+        return vals[0]
+    A = np.stack([np.ones(len(dtaus)), np.asarray(dtaus, dtype=np.float64) ** 2], axis=1)
+    coef = np.linalg.lstsq(A, vals.reshape(len(dtaus), -1), rcond=None)[0]
+    return coef[0].reshape(M + 1, -1)
 
 
 # ---------------------------------------------------------------------------

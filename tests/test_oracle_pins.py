@@ -471,3 +471,95 @@ def test_mc_double_occupancy_and_kinetic_energy_vs_exact():
     assert abs(mean[1] - F.docc()) < 4 * err[1]
     assert abs(mean[2] - F.ekin()) < 4 * err[2]
     assert np.allclose(s[..., 0], 1.0, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# dtau -> 0 extrapolation of G_k(tau) (Sec. 3, Fig. 2).
+# --------------------------------------------------------------------------
+def test_trotter_extrapolation_exact_for_cubic_data():
+    """Runs whose data are cubics in tau with an exactly quadratic dtau
+    dependence, y = P(tau) + Q(tau) dtau^2 plus chain noise that averages to
+    zero: the not-a-knot spline reproduces cubics and the fit in dtau^2 is
+    exact, so the result is P on the fine grid.  A natural spline, a fit in
+    dtau, a shifted grid or a skipped chain average would all miss."""
+    rng = np.random.default_rng(3)
+    beta, N, C, M = 2.0, 5, 4, 37
+    P = rng.standard_normal((4, N))
+    Q = rng.standard_normal((4, N))
+    cubic = lambda c, tau: sum(c[p][None, :] * tau[:, None] ** p for p in range(4))
+    dts = [0.4, 0.2, 0.1]
+    gks = []
+    for dt in dts:
+        tau = np.arange(int(round(beta / dt)) + 1) * dt
+        y = cubic(P, tau) + cubic(Q, tau) * dt ** 2
+        noise = rng.standard_normal((C, len(tau), N))
+        gks.append(y[None] + noise - noise.mean(axis=0, keepdims=True))
+    taus = np.arange(M + 1) * beta / M
+    got = o.trotter_extrapolate(dts, gks, beta, M)
+    np.testing.assert_allclose(got, cubic(P, taus), rtol=0, atol=1e-11)
+    one = o.trotter_extrapolate(dts[:1], gks[:1], beta, M)
+    np.testing.assert_allclose(one, cubic(P, taus) + cubic(Q, taus) * 0.16, rtol=0, atol=1e-11)
+
+
+def test_trotter_extrapolation_u0_closed_form():
+    """U = 0 has no Trotter error: runs sampled from the closed form
+    G_k(tau) = e^{-tau eps_k} / (1 + e^{-beta eps_k}) at three time steps
+    extrapolate to the closed form on the fine grid (spline error only)."""
+    Lx, Ly, beta, M = 4, 4, 4.0, 64
+    eps = o.dispersion(Lx, Ly, 0.25)
+    closed = lambda tau: np.exp(-tau[:, None] * eps[None, :]) / (1.0 + np.exp(-beta * eps[None, :]))
+    dts = [0.1, 0.05, 0.025]
+    gks = [closed(np.arange(int(round(beta / dt)) + 1) * dt)[None] for dt in dts]
+    got = o.trotter_extrapolate(dts, gks, beta, M)
+    # cubic-spline error on a uniform grid: (5/384) h^4 max|d^4 G/d tau^4|, at most
+    # (5/384) h^4 max|eps|^4 = 1.3e-6 for the coarsest run (h = 0.1, |eps| <= 4t = 1);
+    # the fit weights of the three runs sum to 1 with absolute sum 4/3
+    bound = (4.0 / 3.0) * (5.0 / 384.0) * dts[0] ** 4 * np.max(np.abs(eps)) ** 4
+    np.testing.assert_allclose(got, closed(np.arange(M + 1) * beta / M), rtol=0, atol=bound)
+
+
+def _gk_from_gij(G, Lx, Ly):
+    N = Lx * Ly
+    out = np.zeros(N)
+    for ky in range(Ly):
+        for kx in range(Lx):
+            acc = 0.0
+            for i in range(N):
+                for j in range(N):
+                    dx, dy = i % Lx - j % Lx, i // Lx - j // Lx
+                    acc += math.cos(2 * math.pi * (kx * dx / Lx + ky * dy / Ly)) * G[i, j]
+            out[kx + Lx * ky] = acc / N
+    return out
+
+
+def test_trotter_extrapolation_removes_fock_trotter_error():
+    """2x2 Hubbard cluster at U = 2: Trotterised G_k(tau) from the Fock-space
+    transfer matrices at L = 8, 12, 16, extrapolated, against the exact
+    continuous-time Tr[e^{-(beta-tau)H} c_k e^{-tau H} c_k^dag] / Z.  The raw
+    error falls like dtau^2; the extrapolation removes it to O(dtau^4) where
+    all grids have points, and to spline accuracy in between."""
+    Lx, Ly, t, U, beta, M = 2, 2, 0.25, 2.0, 2.0, 48
+    N = Lx * Ly
+    dts, gks = [], []
+    for L in (8, 12, 16):
+        F = fock.FockHubbard(Lx, Ly, t, U, beta / L, L)
+        dts.append(beta / L)
+        gks.append(np.array([_gk_from_gij(F.gtau_up(l), Lx, Ly) for l in range(L + 1)])[None])
+    H = F.Ht + np.diag(U * np.sum((F.nu - 0.5) * (F.nd - 0.5), axis=1))
+    w, v = np.linalg.eigh(H)
+    eH = lambda a: (v * np.exp(-a * w)) @ v.T
+    Z = np.sum(np.exp(-beta * w))
+    cs = [F.c_up(i) for i in range(N)]
+    taus = np.arange(M + 1) * beta / M
+    exact = []
+    for tau in taus:
+        A, B = eH(beta - tau), eH(tau)
+        G = np.array([[np.trace(A @ cs[i] @ B @ cs[j].T) for j in range(N)] for i in range(N)]) / Z
+        exact.append(_gk_from_gij(G, Lx, Ly))
+    exact = np.array(exact)
+    raw = [np.max(np.abs(o.trotter_extrapolate([d], [g], beta, M) - exact)) for d, g in zip(dts, gks)]
+    assert raw[0] / raw[2] == pytest.approx((dts[0] / dts[2]) ** 2, rel=0.1)  # dtau^2 error
+    got = o.trotter_extrapolate(dts, gks, beta, M)
+    nodes = [0, 12, 24, 36, 48]  # tau = 0, 0.5, 1, 1.5, 2 lie on every grid
+    assert np.max(np.abs(got[nodes] - exact[nodes])) < raw[2] / 20
+    assert np.max(np.abs(got - exact)) < raw[2] / 4
