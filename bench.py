@@ -443,6 +443,69 @@ def config_groups(pkg, name, precision):
     raise ValueError(name)
 
 
+def time_extrapolation(pkg, torch, groups, gbuf, reps, M=400):
+    """dtau -> 0 extrapolation of G_k(tau) over the groups' runs (one group per
+    dtau, same lattice and beta), from the device buffer dqmc_measure_Gtau
+    filled; L2 is flushed before every timed call.  Bound: HBM, the chain
+    data read once (the chain average dominates)."""
+    views, off = [], 0
+    for g in groups:
+        n = g.n_chains * (g.L + 1) * g.N
+        views.append(gbuf[off:off + n].view(g.n_chains, g.L + 1, g.N))
+        off += n
+    dts = [g.dtau for g in groups]
+    beta = groups[0].beta
+    # L2 flush by reading 2x the 129 MB L2 (a written buffer would leave dirty
+    # lines whose write-back the timed kernel would pay for)
+    flush = torch.zeros(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        pkg.trotter_extrapolate(dts, views, beta, M)
+    ms, kms = [], []
+    for _ in range(reps):
+        flush.sum()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pkg.trotter_extrapolate(dts, views, beta, M)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        kms.append(pkg.trotter_timing())
+    med = lambda v: sorted(v)[len(v) // 2]
+    ms = med(ms)
+    k_mean, k_spline, k_fit = (med([k[q] for k in kms]) for q in range(3))
+    in_bytes = off * 8  # the chain data, read once by the chain average
+    nbytes = in_bytes + (M + 1) * groups[0].N * 8
+    peak = measured_peaks().get("hbm_gbs")
+    gbs = in_bytes / (k_mean / 1e3) / 1e9  # dominant kernel: the chain average
+    return {"workload": "%d runs, dtau %s, %d chains x (L+1) x %d momenta each, M = %d"
+                        % (len(groups), "/".join("%g" % d for d in dts), groups[0].n_chains,
+                           groups[0].N, M),
+            "call_ms_median": ms, "call_gbs": nbytes / (ms / 1e3) / 1e9,
+            "kernel_ms_median": {"chain_mean": k_mean, "spline": k_spline, "fit": k_fit},
+            "roofline": {"kernel": "chain_mean", "bound": "hbm", "achieved": gbs, "unit": "GB/s",
+                         "peak": peak, "frac": gbs / peak if peak else None,
+                         "traffic": None, "bytes_per_launch": in_bytes,
+                         "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"
+                         if peak else None},
+            "l2": "flushed before every call (256 MB read)"}
+
+
+def run_trotter(args):
+    """The dtau -> 0 extrapolation alone, on seeded synthetic runs shaped like
+    the 8x8 three-dtau configuration (256 chains per run, G_k(tau) on L + 1 =
+    51 / 101 / 201 slices, 64 momenta), resident on the device."""
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    groups = config_groups(pkg, "c2", "fp64")
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    total = sum(g.n_chains * (g.L + 1) * g.N for g in groups)
+    gbuf = torch.rand(total, dtype=torch.float64, device="cuda", generator=gen)
+    line = {"leg": "trotter_extrapolate", "data": "synthetic"}
+    line.update(time_extrapolation(pkg, torch, groups, gbuf, max(5, args.steps)))
+    print(json.dumps(line), flush=True)
+
+
 def run_config(args):
     """One JSON line per precision for a secondary configuration: sweeps (with
     G(tau) for c2/c4, with the gradient for c5) per second and updates/s."""
@@ -481,10 +544,14 @@ def run_config(args):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / args.steps
             d, a = sim.stats()
-            print(json.dumps({"config": args.config, "precision": prec, "ms_per_step": ms,
-                              "updates_per_s": n_up / (ms / 1e3), "chains": sim.n_chains,
-                              "drift_max": float(d.max()), "autotune": tuned,
-                              "acceptance": float(a.sum()) / (n_up * args.steps)}), flush=True)
+            line = {"config": args.config, "precision": prec, "ms_per_step": ms,
+                    "updates_per_s": n_up / (ms / 1e3), "chains": sim.n_chains,
+                    "drift_max": float(d.max()), "autotune": tuned,
+                    "acceptance": float(a.sum()) / (n_up * args.steps)}
+            if args.config == "c2":
+                line["trotter_extrapolate"] = time_extrapolation(pkg, torch, groups, gbuf,
+                                                                 max(5, args.steps))
+            print(json.dumps(line), flush=True)
 
 
 def bench_config():
@@ -542,6 +609,8 @@ def main():
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
     ap.add_argument("--scan-ns", action="store_true",
                     help="print the G drift against the stabilisation interval and exit")
+    ap.add_argument("--trotter", action="store_true",
+                    help="time the dtau -> 0 extrapolation of G_k(tau) alone and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -551,6 +620,8 @@ def main():
         run_profile_case(args)
     elif args.scan_ns:
         run_scan_ns(args)
+    elif args.trotter:
+        run_trotter(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

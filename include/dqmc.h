@@ -60,6 +60,7 @@ extern "C" {
 /* Limits of this build. */
 #define DQMC_MAX_SIDE 16  /* Lx, Ly <= 16, so N <= 256                          */
 #define DQMC_MAX_DELAY 32 /* delay_k <= 32                                       */
+#define DQMC_TX_MAX_RUNS 16 /* runs per dqmc_trotter_extrapolate call           */
 
 /* One group of chains with identical parameters (Eqs. (1)-(2)). */
 typedef struct {
@@ -145,6 +146,36 @@ int dqmc_recompute_G(dqmc_ctx* ctx, double* max_drift_out);
  * Requires current UDV stacks (true after dqmc_init, dqmc_sweep,
  * dqmc_set_field and dqmc_recompute_G). */
 int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device);
+
+/* dtau -> 0 extrapolation of G_k(tau) (Sec. 3, Fig. 2): runs at different
+ * Trotter steps, each on its own grid tau_l = l dtau[r], are averaged over
+ * their chains, put on the common fine grid tau_m = m beta / M (m = 0..M) by
+ * the not-a-knot cubic spline through each run's L[r] + 1 points (the paper
+ * does not name its spline; this is the reading taken), and fitted at every
+ * (tau_m, k) by least squares to a + b dtau^2; out[m][k] = a.  With R = 1 the
+ * result is the run's interpolation.
+ *   R        1..DQMC_TX_MAX_RUNS runs; for R >= 2 the dtau must not all be equal
+ *   dtau, L, C  host arrays [R]: time step, slices (L[r] >= 3, L[r] dtau[r] =
+ *            beta to 1e-9) and chain count of each run
+ *   gk       host array [R] of pointers to [C[r]][L[r] + 1][N] doubles, the
+ *            layout dqmc_measure_Gtau writes for one group
+ *   N        momenta per row (N of the lattice)
+ *   out      [M + 1][N] doubles, caller-owned
+ * The gk data and out are device pointers if on_device, else host.  FP64;
+ * stateless (no context); runs on the legacy default stream and synchronises
+ * it before returning, so device inputs written on other streams must be
+ * complete.  Keeps a scratch buffer per device between calls (grown when a
+ * call needs more, released at process exit); concurrent calls are
+ * serialised.  Errors: DQMC_ERR_ARG, DQMC_ERR_OOM, DQMC_ERR_CUDA. */
+int dqmc_trotter_extrapolate(int R, const double* dtau, const int* L, const int* C,
+                             const double* const* gk, int N, double beta, int M, double* out,
+                             int on_device);
+
+/* Device time in ms of the three kernels of the last dqmc_trotter_extrapolate
+ * call on the current device (chain average, spline, interpolation and fit),
+ * from CUDA events recorded around them: host array ms_out[3].  Zeros before
+ * the first call.  Errors: DQMC_ERR_ARG, DQMC_ERR_CUDA. */
+int dqmc_trotter_timing(float* ms_out);
 int64_t dqmc_gtau_size(const dqmc_ctx* ctx);
 
 /* Derivatives of log W = log|det M_up| + log|det M_dn| (Eq. (3)) of the

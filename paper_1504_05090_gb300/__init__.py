@@ -250,6 +250,47 @@ def autotune(groups, drift_target=1e-6, seed=0):
     return res
 
 
+def trotter_extrapolate(dtaus, gks, beta, M):
+    """dtau -> 0 extrapolation of G_k(tau) (see dqmc_trotter_extrapolate).
+    gks[r]: run r's G_k(tau_l) per chain, shape [C, L + 1, N], as returned by
+    DQMC.gtau() for one group: all numpy arrays (host) or all CUDA tensors
+    (device).  Returns [M + 1, N] on the same side as the inputs."""
+    R = len(gks)
+    if R != len(dtaus) or R < 1:
+        raise ValueError("one dtau per run")
+    on_dev = all(hasattr(g, "is_cuda") and g.is_cuda for g in gks)
+    if on_dev:
+        import torch
+        gks = [g.contiguous().to(torch.float64) for g in gks]
+    else:
+        gks = [np.ascontiguousarray(g, dtype=np.float64) for g in gks]
+    shapes = [tuple(g.shape) for g in gks]
+    N = shapes[0][2]
+    if any(len(s) != 3 or s[2] != N for s in shapes):
+        raise ValueError("each run must be [chains, L + 1, N] with the same N")
+    dt = np.ascontiguousarray(dtaus, dtype=np.float64)
+    L = np.array([s[1] - 1 for s in shapes], dtype=np.int32)
+    C = np.array([s[0] for s in shapes], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * R)(*[_ptr(g).value for g in gks])
+    if on_dev:
+        torch.cuda.current_stream().synchronize()
+        out = torch.empty((M + 1, N), dtype=torch.float64, device=gks[0].device)
+    else:
+        out = np.empty((M + 1, N))
+    _lib.check(lib().dqmc_trotter_extrapolate(R, _ptr(dt), _ptr(L), _ptr(C), ptrs, int(N),
+                                              float(beta), int(M), _ptr(out), int(on_dev)),
+               "dqmc_trotter_extrapolate", lib())
+    return out
+
+
+def trotter_timing():
+    """Device ms of the three kernels of the last trotter_extrapolate call on
+    the current device: (chain average, spline, interpolation and fit)."""
+    out = np.zeros(3, dtype=np.float32)
+    _lib.check(lib().dqmc_trotter_timing(_ptr(out)), "dqmc_trotter_timing", lib())
+    return tuple(float(v) for v in out)
+
+
 class LogWeight:
     """torch.autograd.Function: log W = log|det M_up| + log|det M_dn| of the
     current field of every chain as a function of (t, lambda).  The forward

@@ -67,6 +67,11 @@ SIGNATURES = {
     "dqmc_timing_class_name": (ctypes.c_char_p, [ctypes.c_int]),
     "dqmc_green_noalloc": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    "dqmc_trotter_extrapolate": (ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                                                ctypes.c_int]),
+    "dqmc_trotter_timing": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_destroy": (None, [ctypes.c_void_p]),
     "dqmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dqmc_last_cuda_error": (ctypes.c_char_p, [ctypes.POINTER(ctypes.c_int)]),

@@ -65,3 +65,31 @@ def test_package_fails_loudly_without_library(tmp_path):
     from paper_1504_05090_gb300 import _lib
     with pytest.raises(ImportError):
         _lib.load(str(tmp_path / "missing.so"))
+
+
+def test_trotter_extrapolate_argument_checks_without_gpu(libpath):
+    """dqmc_trotter_extrapolate rejects bad runs before any CUDA call."""
+    import numpy as np
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    buf = np.zeros(4 * 9 * 2)
+    out = np.zeros(5 * 2)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+
+    def call(R, dts, Ls, Cs, N=2, beta=2.0, M=4, null_run=False):
+        dt = np.array(dts, dtype=np.float64)
+        L = np.array(Ls, dtype=np.int32)
+        C = np.array(Cs, dtype=np.int32)
+        ptrs = (ctypes.c_void_p * max(R, 1))(*([None if null_run else buf.ctypes.data] * max(R, 1)))
+        return lib.dqmc_trotter_extrapolate(R, P(dt), P(L), P(C), ptrs, N, beta, M, P(out), 0)
+
+    assert call(0, [0.25], [8], [1]) == -1                      # no runs
+    assert call(17, [0.25] * 17, [8] * 17, [1] * 17) == -1      # more than DQMC_TX_MAX_RUNS
+    assert call(1, [1.0], [2], [1]) == -1                       # L < 3
+    assert call(1, [0.25], [7], [1]) == -1                      # L dtau != beta
+    assert call(2, [0.25, 0.25], [8, 8], [1, 1]) == -1          # all dtau equal
+    assert call(1, [0.25], [8], [0]) == -1                      # no chains
+    assert call(1, [0.25], [8], [1], null_run=True) == -1       # missing data
+    assert call(1, [0.25], [8], [1], N=0) == -1
+    assert call(1, [0.25], [8], [1], M=0) == -1
+    assert call(1, [0.25], [8], [1], beta=-2.0) == -1
