@@ -61,6 +61,13 @@ points the paper leaves open:
       extrapolation is a least-squares fit in dtau^2, the order of the
       Trotter error of the momentum-diagonal G_k(tau) (the K/V split is
       similar to the symmetric one there).
+  R16 Matsubara transform (Eq. 5) and Dyson equation (Eq. 6): the transform
+      is taken of the standard-sign G(tau) = -<T c(tau) c^dag> (the negative
+      of R7's) with kernel e^{+i w_n tau}, which is what makes Eq. 6 give
+      Sigma = 0 at U = 0; the printed exponent e^{-i w_n tau} with either
+      sign of G would leave Sigma = 2 i w_n or -2 eps_k there.  mu = 0 (half
+      filling with the (n - 1/2) form of Eq. 1).  The quasi-continuous G(tau)
+      between samples is the not-a-knot cubic spline of R15.
 """
 from __future__ import annotations
 
@@ -77,6 +84,7 @@ __all__ = [
     "n_slices", "b_matrix", "b_inverse", "udv_chain", "green_from_udv",
     "two_stack_green", "Params", "Chain", "observables_from_g",
     "spin_correlation_from_g", "momentum_diag", "weight_log", "trotter_extrapolate",
+    "matsubara_sigma",
 ]
 
 MASK32 = 0xFFFFFFFF
@@ -384,6 +392,38 @@ def trotter_extrapolate(dtaus, gks, beta, M):
     A = np.stack([np.ones(len(dtaus)), np.asarray(dtaus, dtype=np.float64) ** 2], axis=1)
     coef = np.linalg.lstsq(A, vals.reshape(len(dtaus), -1), rcond=None)[0]
     return coef[0].reshape(M + 1, -1)
+
+
+# ---------------------------------------------------------------------------
+# Matsubara Green function and self-energy (Sec. 3, Eqs. 5-6; reading R16).
+# ---------------------------------------------------------------------------
+def matsubara_sigma(gk, beta, Lx, Ly, t, n_freq, nodes=12):
+    """G_k(i w_n) and Sigma_k(i w_n), w_n = (2n + 1) pi / beta, n < n_freq,
+    from G_k(tau) sampled on tau_m = m beta / M (gk [M + 1, N], the
+    non-negative convention <c_k(tau) c_k^dag> of R7, e.g. the output of
+    trotter_extrapolate).  Steps, in the order of Eqs. 5-6: the not-a-knot
+    cubic spline S_k(tau) through the samples; the standard-sign transform
+      G_k(i w_n) = - int_0^beta S_k(tau) e^{i w_n tau} dtau,
+    each grid interval integrated by Gauss-Legendre quadrature with `nodes`
+    points (exact to rounding while w_n h stays of order a few); the Dyson
+    equation at half filling (mu = 0),
+      Sigma_k(i w_n) = i w_n - eps_k - 1 / G_k(i w_n).
+    Returns (G [n_freq, N], Sigma [n_freq, N]), complex."""
+    gk = np.asarray(gk, dtype=np.float64)
+    M = gk.shape[0] - 1
+    h = beta / M
+    spline = scipy.interpolate.CubicSpline(np.arange(M + 1) * h, gk, axis=0, bc_type="not-a-knot")
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    tau = (np.arange(M)[:, None] * h + 0.5 * h * (x[None, :] + 1.0)).reshape(-1)  # all nodes
+    wt = np.tile(0.5 * h * w, M)
+    S = spline(tau)  # [M * nodes, N]
+    wn = (2 * np.arange(n_freq) + 1) * np.pi / beta
+    G = np.empty((n_freq, gk.shape[1]), dtype=np.complex128)
+    for n in range(n_freq):
+        G[n] = -np.sum((wt * np.exp(1j * wn[n] * tau))[:, None] * S, axis=0)
+    eps = dispersion(Lx, Ly, t)
+    sigma = 1j * wn[:, None] - eps[None, :] - 1.0 / G
+    return G, sigma
 
 
 # ---------------------------------------------------------------------------

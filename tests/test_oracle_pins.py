@@ -563,3 +563,86 @@ def test_trotter_extrapolation_removes_fock_trotter_error():
     nodes = [0, 12, 24, 36, 48]  # tau = 0, 0.5, 1, 1.5, 2 lie on every grid
     assert np.max(np.abs(got[nodes] - exact[nodes])) < raw[2] / 20
     assert np.max(np.abs(got - exact)) < raw[2] / 4
+
+
+# --------------------------------------------------------------------------
+# Matsubara transform and Dyson self-energy (Sec. 3, Eqs. 5-6).
+# --------------------------------------------------------------------------
+def test_matsubara_transform_exact_for_cubic_data():
+    """Samples of a cubic G(tau): the spline is the cubic itself, so the
+    transform equals -int_0^beta p(tau) e^{i w tau} dtau, written here by
+    integration by parts, [e^{a tau} (p/a - p'/a^2 + p''/a^3 - p'''/a^4)]_0^beta
+    with a = i w_n."""
+    rng = np.random.default_rng(5)
+    beta, M, N, nf = 3.0, 60, 3, 40
+    c = rng.standard_normal((4, N))
+    tau = np.arange(M + 1) * beta / M
+    g = sum(c[p][None, :] * tau[:, None] ** p for p in range(4))
+    G, _ = o.matsubara_sigma(g, beta, N, 1, 0.25, nf)
+    for n in range(nf):
+        a = 1j * (2 * n + 1) * np.pi / beta
+        def prim(x):
+            p0 = c[0] + c[1] * x + c[2] * x ** 2 + c[3] * x ** 3
+            p1 = c[1] + 2 * c[2] * x + 3 * c[3] * x ** 2
+            p2 = 2 * c[2] + 6 * c[3] * x
+            p3 = 6 * c[3]
+            return np.exp(a * x) * (p0 / a - p1 / a ** 2 + p2 / a ** 3 - p3 / a ** 4)
+        exact = -(prim(beta) - prim(0.0))
+        np.testing.assert_allclose(G[n], exact, rtol=1e-12, atol=1e-13 * np.max(np.abs(exact)))
+
+
+def test_matsubara_sigma_vanishes_at_u0():
+    """U = 0: G_k(tau) = e^{-tau eps_k} / (1 + e^{-beta eps_k}) transforms to
+    1 / (i w_n - eps_k) and Eq. 6 gives Sigma = 0, up to the spline error:
+    |dG(i w)| <= beta max|dS| with |dS| <= (5/384) h^4 max|eps|^4, and
+    |dSigma| = |dG| / |G|^2 <= |dG| (w^2 + eps^2) to first order."""
+    Lx, Ly, t, beta, M, nf = 4, 4, 0.25, 10.0, 1000, 24
+    eps = o.dispersion(Lx, Ly, t)
+    tau = np.arange(M + 1) * beta / M
+    g = np.exp(-tau[:, None] * eps[None, :]) / (1.0 + np.exp(-beta * eps[None, :]))
+    G, sigma = o.matsubara_sigma(g, beta, Lx, Ly, t, nf)
+    wn = (2 * np.arange(nf) + 1) * np.pi / beta
+    np.testing.assert_allclose(G, 1.0 / (1j * wn[:, None] - eps[None, :]), rtol=0, atol=1e-7)
+    dG = beta * 5.0 / 384.0 * (beta / M) ** 4 * np.max(np.abs(eps)) ** 4
+    bound = 2.0 * dG * (wn[:, None] ** 2 + eps[None, :] ** 2) + 1e-12
+    assert np.all(np.abs(sigma) <= bound)
+
+
+def test_matsubara_sigma_2x2_hubbard_vs_lehmann():
+    """2x2 cluster at U = 2: the exact continuous-time G_k(tau) of the Fock
+    space, sampled on a fine grid and transformed, against the Lehmann sum
+    G_k(i w) = (1/Z) sum_ab |<b|c_k^dag|a>|^2 (e^{-beta E_a} + e^{-beta E_b})
+    / (i w - (E_b - E_a)).  Sigma is then exact up to the spline error, and
+    Re Sigma vanishes at k = (pi, 0), where eps_k = 0 (particle-hole)."""
+    Lx, Ly, t, U, beta, M, nf = 2, 2, 0.25, 2.0, 2.0, 400, 12
+    N = Lx * Ly
+    F = fock.FockHubbard(Lx, Ly, t, U, beta, 1)
+    H = F.Ht + np.diag(U * np.sum((F.nu - 0.5) * (F.nd - 0.5), axis=1))
+    E, V = np.linalg.eigh(H)
+    Z = np.sum(np.exp(-beta * E))
+    cs = [F.c_up(i) for i in range(N)]
+    tau = np.arange(M + 1) * beta / M
+    wn = (2 * np.arange(nf) + 1) * np.pi / beta
+    g = np.zeros((M + 1, N))
+    Gex = np.zeros((nf, N), dtype=np.complex128)
+    for ky in range(Ly):
+        for kx in range(Lx):
+            k = kx + Lx * ky
+            phase = [np.exp(-2j * np.pi * (kx * (j % Lx) / Lx + ky * (j // Lx) / Ly)) for j in range(N)]
+            ck = sum(phase[j] * cs[j] for j in range(N)) / np.sqrt(N)
+            C = V.T @ ck @ V                   # <a| c_k |b>
+            A2 = np.abs(C) ** 2
+            # our G_k(tau) = (1/Z) sum_ab e^{-(beta - tau) E_a} |<a|c_k|b>|^2 e^{-tau E_b}
+            for m, tt in enumerate(tau):
+                g[m, k] = np.sum(np.exp(-(beta - tt) * E)[:, None] * A2 * np.exp(-tt * E)[None, :]) / Z
+            # Lehmann with c_k^dag: <b|c_k^dag|a> = conj(<a|c_k|b>)
+            boltz = np.exp(-beta * E)[:, None] + np.exp(-beta * E)[None, :]
+            for n in range(nf):
+                Gex[n, k] = np.sum(A2 * boltz / (1j * wn[n] - (E[None, :] - E[:, None]))) / Z
+    G, sigma = o.matsubara_sigma(g, beta, Lx, Ly, t, nf)
+    np.testing.assert_allclose(G, Gex, rtol=0, atol=1e-9)
+    eps = o.dispersion(Lx, Ly, t)
+    sig_ex = 1j * wn[:, None] - eps[None, :] - 1.0 / Gex
+    np.testing.assert_allclose(sigma, sig_ex, rtol=0, atol=1e-6)
+    assert np.max(np.abs(sig_ex)) > 0.05                 # the interaction is visible
+    assert np.max(np.abs(sigma[:, 1].real)) < 1e-9       # k = (pi, 0)
