@@ -491,6 +491,38 @@ def time_extrapolation(pkg, torch, groups, gbuf, reps, M=400):
             "l2": "flushed before every call (256 MB read)"}
 
 
+def time_matsubara(pkg, torch, fine, g, beta, reps, n_freq=200):
+    """Matsubara transform and Dyson self-energy of the extrapolated G_k(tau)
+    (device tensor [M + 1, N]) for n_freq frequencies.  Bound: the FP64 pipe;
+    the transform does 8 FP64 flops per (frequency, momentum, knot): the
+    sums of z_j y_j and z_j M_j, four FMAs."""
+    M = fine.shape[0] - 1
+    for _ in range(3):
+        pkg.matsubara_sigma(fine, beta, g.Lx, g.Ly, g.t, n_freq)
+    ms, kms = [], []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        pkg.matsubara_sigma(fine, beta, g.Lx, g.Ly, g.t, n_freq)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        kms.append(pkg.matsubara_timing())
+    med = lambda v: sorted(v)[len(v) // 2]
+    k_spline, k_transform = (med([k[q] for k in kms]) for q in range(2))
+    flops = 8.0 * n_freq * g.N * M
+    tf = flops / (k_transform / 1e3) / 1e12
+    return {"workload": "G_k(tau) on M = %d intervals, %d momenta, %d Matsubara frequencies"
+                        % (M, g.N, n_freq),
+            "call_ms_median": med(ms),
+            "kernel_ms_median": {"spline": k_spline, "transform_and_dyson": k_transform},
+            "roofline": {"kernel": "transform_and_dyson", "bound": "alu", "achieved": tf,
+                         "unit": "TFLOP/s", "peak": FP64_PEAK, "frac": tf / FP64_PEAK,
+                         "flops_per_launch": flops,
+                         "peak_source": "derived FP64 pipe: 152 SMs x 2 FMA/clk x 2 x 2070 MHz"}}
+
+
 def run_trotter(args):
     """The dtau -> 0 extrapolation alone, on seeded synthetic runs shaped like
     the 8x8 three-dtau configuration (256 chains per run, G_k(tau) on L + 1 =
@@ -503,6 +535,14 @@ def run_trotter(args):
     gbuf = torch.rand(total, dtype=torch.float64, device="cuda", generator=gen)
     line = {"leg": "trotter_extrapolate", "data": "synthetic"}
     line.update(time_extrapolation(pkg, torch, groups, gbuf, max(5, args.steps)))
+    views, off = [], 0
+    for g in groups:
+        n = g.n_chains * (g.L + 1) * g.N
+        views.append(gbuf[off:off + n].view(g.n_chains, g.L + 1, g.N))
+        off += n
+    fine = pkg.trotter_extrapolate([g.dtau for g in groups], views, groups[0].beta, 400)
+    line["matsubara_sigma"] = time_matsubara(pkg, torch, fine, groups[0], groups[0].beta,
+                                             max(5, args.steps))
     print(json.dumps(line), flush=True)
 
 

@@ -176,6 +176,30 @@ int dqmc_trotter_extrapolate(int R, const double* dtau, const int* L, const int*
  * from CUDA events recorded around them: host array ms_out[3].  Zeros before
  * the first call.  Errors: DQMC_ERR_ARG, DQMC_ERR_CUDA. */
 int dqmc_trotter_timing(float* ms_out);
+
+/* Matsubara Green function (Eq. 5) and self-energy from the Dyson equation
+ * (Eq. 6) at half filling (mu = 0):
+ *   G_k(i w_n) = -int_0^beta S_k(tau) e^{i w_n tau} dtau,  w_n = (2n+1) pi / beta,
+ *   Sigma_k(i w_n) = i w_n - eps_k - 1 / G_k(i w_n),  eps_k = -2t (cos kx + cos ky),
+ * where S_k is the not-a-knot cubic spline through the samples gk[m][k] =
+ * G_k(tau_m) >= 0 (the convention of dqmc_measure_Gtau) on tau_m = m beta / M,
+ * integrated exactly (the minus sign gives the standard G = -<T c c^dag>;
+ * the exponent is the one under which Eq. 6 gives Sigma = 0 at U = 0).
+ *   gk       [M + 1][N] doubles, N = Lx * Ly, k = kx + Lx ky (for instance the
+ *            output of dqmc_trotter_extrapolate); M >= 3
+ *   n_freq   frequencies n = 0..n_freq-1
+ *   g_iw     [n_freq][N] complex (re, im interleaved) or NULL
+ *   sigma    [n_freq][N] complex (re, im interleaved)
+ * Pointers are device pointers if on_device, else host.  FP64, stateless,
+ * on the legacy default stream (synchronised before returning); shares the
+ * scratch and serialisation of dqmc_trotter_extrapolate.  Errors:
+ * DQMC_ERR_ARG, DQMC_ERR_OOM, DQMC_ERR_CUDA. */
+int dqmc_matsubara_sigma(const double* gk, int M, int Lx, int Ly, double t, double beta,
+                         int n_freq, double* g_iw, double* sigma, int on_device);
+
+/* Device time in ms of the last dqmc_matsubara_sigma call on the current
+ * device: ms_out[0] the spline, ms_out[1] the transform and Dyson step. */
+int dqmc_matsubara_timing(float* ms_out);
 int64_t dqmc_gtau_size(const dqmc_ctx* ctx);
 
 /* Derivatives of log W = log|det M_up| + log|det M_dn| (Eq. (3)) of the

@@ -291,6 +291,42 @@ def trotter_timing():
     return tuple(float(v) for v in out)
 
 
+def matsubara_sigma(gk, beta, Lx, Ly, t, n_freq):
+    """(G_k(i w_n), Sigma_k(i w_n)) for n < n_freq from G_k(tau_m) on
+    tau_m = m beta / M (see dqmc_matsubara_sigma).  gk: [M + 1, Lx*Ly], a numpy
+    array (host; complex numpy results) or a CUDA tensor (complex CUDA
+    tensors)."""
+    on_dev = hasattr(gk, "is_cuda") and gk.is_cuda
+    if on_dev:
+        import torch
+        gk = gk.contiguous().to(torch.float64)
+    else:
+        gk = np.ascontiguousarray(gk, dtype=np.float64)
+    M, N = gk.shape[0] - 1, gk.shape[1]
+    if N != Lx * Ly:
+        raise ValueError("gk must have Lx * Ly columns")
+    if on_dev:
+        g = torch.empty((n_freq, N, 2), dtype=torch.float64, device=gk.device)
+        s = torch.empty_like(g)
+        torch.cuda.current_stream().synchronize()
+    else:
+        g = np.empty((n_freq, N, 2))
+        s = np.empty((n_freq, N, 2))
+    _lib.check(lib().dqmc_matsubara_sigma(_ptr(gk), int(M), int(Lx), int(Ly), float(t),
+                                          float(beta), int(n_freq), _ptr(g), _ptr(s), int(on_dev)),
+               "dqmc_matsubara_sigma", lib())
+    if on_dev:
+        return torch.view_as_complex(g), torch.view_as_complex(s)
+    return g[..., 0] + 1j * g[..., 1], s[..., 0] + 1j * s[..., 1]
+
+
+def matsubara_timing():
+    """Device ms of the last matsubara_sigma call: (spline, transform)."""
+    out = np.zeros(2, dtype=np.float32)
+    _lib.check(lib().dqmc_matsubara_timing(_ptr(out)), "dqmc_matsubara_timing", lib())
+    return tuple(float(v) for v in out)
+
+
 class LogWeight:
     """torch.autograd.Function: log W = log|det M_up| + log|det M_dn| of the
     current field of every chain as a function of (t, lambda).  The forward

@@ -72,6 +72,10 @@ SIGNATURES = {
                                                 ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
                                                 ctypes.c_int]),
     "dqmc_trotter_timing": (ctypes.c_int, [ctypes.c_void_p]),
+    "dqmc_matsubara_sigma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "dqmc_matsubara_timing": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_destroy": (None, [ctypes.c_void_p]),
     "dqmc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "dqmc_last_cuda_error": (ctypes.c_char_p, [ctypes.POINTER(ctypes.c_int)]),

@@ -93,3 +93,28 @@ def test_trotter_extrapolate_argument_checks_without_gpu(libpath):
     assert call(1, [0.25], [8], [1], N=0) == -1
     assert call(1, [0.25], [8], [1], M=0) == -1
     assert call(1, [0.25], [8], [1], beta=-2.0) == -1
+
+
+def test_matsubara_sigma_argument_checks_without_gpu(libpath):
+    """dqmc_matsubara_sigma rejects bad sizes before any CUDA call."""
+    import numpy as np
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    g = np.zeros((9, 4))
+    out = np.zeros((3, 4, 2))
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    ok = dict(M=8, Lx=2, Ly=2, t=0.25, beta=2.0, nf=3)
+
+    def call(gk=g, sig=out, **kw):
+        a = dict(ok, **kw)
+        return lib.dqmc_matsubara_sigma(None if gk is None else P(gk), a["M"], a["Lx"], a["Ly"],
+                                        a["t"], a["beta"], a["nf"], None,
+                                        None if sig is None else P(sig), 0)
+
+    assert call(gk=None) == -1
+    assert call(sig=None) == -1
+    assert call(M=2) == -1
+    assert call(Lx=0) == -1
+    assert call(beta=0.0) == -1
+    assert call(nf=0) == -1
+    assert call(t=float("nan")) == -1
