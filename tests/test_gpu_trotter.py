@@ -42,6 +42,7 @@ def _runs(seed, beta, Ls, C, N):
     (1.2, (3, 4, 5), 3, 36, 7),             # the smallest grids (L = 3 and 4 take the short paths)
     (0.7, (7,), 1, 5, 13),                  # one run: interpolation only
     (3.6, (4, 9), 2, 100, 1),               # two runs, ragged N, coarse output grid
+    (1.0, (4, 5), 3, 5, 9),                 # odd row length (L + 1) N = 25: element-wise loads
 ])
 def test_extrapolation_matches_oracle_host_and_device(beta, Ls, C, N, M):
     import torch
