@@ -249,7 +249,10 @@ def class_work(cls, acceptance, precision):
     if cls == "qr_pivot":  # Householder R and explicit Q, both stacks
         return "alu64", C * 2 * nc * (8.0 / 3.0) * N ** 3
     if cls == "gj_inverse":  # nc recomputes + (nc + 1) stabilisation points for G(tau)
-        return "alu64", C * (2 * nc + 1) * g3
+        # (float-pair groups invert the G(tau) points in float pairs, the class below)
+        return "alu64", C * (nc if precision == "df32" else 2 * nc + 1) * g3
+    if cls == "gj_inverse_pair":  # G(tau) points of float-pair groups
+        return "alu32x2", C * (nc + 1) * g3
     if cls in ("stack_kron", "gtau_propagate"):
         # two matrices (right and left stack; G(l,0) and Y) x L slices x N vectors
         # x 2N(Lx+Ly) flops per Kronecker application; G(tau) is propagated in

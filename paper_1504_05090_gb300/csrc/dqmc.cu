@@ -99,11 +99,11 @@ using namespace dqmc;
 // Kernel classes for the optional per-launch timing (dqmc_timing_*).
 enum TimingClass : int {
   kTMetropolis = 0, kTWrap, kTStackKron, kTQR, kTGemm, kTInverse, kTGtauProp, kTGtauFinal,
-  kTGrad, kTMisc, kTNumClasses
+  kTGrad, kTInversePair, kTMisc, kTNumClasses
 };
 static const char* kTimingNames[kTNumClasses] = {
     "metropolis", "wrap", "stack_kron", "qr_pivot", "gemm_f64", "gj_inverse", "gtau_propagate",
-    "gtau_finalize", "grad_terms", "misc"};
+    "gtau_finalize", "grad_terms", "gj_inverse_pair", "misc"};
 
 struct dqmc_ctx {
   std::vector<Group> g;
@@ -533,12 +533,14 @@ int check_status(dqmc_ctx* ctx) {
 
 // Stabilised matrices at all stabilisation points of every chain:
 // Mid^{-1} in g.A2 and W1 = U_L Db_L^{-1} Mid^{-1} in g.W1 (g.Mid is overwritten).
-int all_points_w1(dqmc_ctx* ctx, Group& g) {
+// pair: invert the middle matrices in float pairs (G(tau) of float-pair
+// groups, where log|det| is not needed); FP64 otherwise.
+int all_points_w1(dqmc_ctx* ctx, Group& g, bool pair) {
   const int batch = g.C * (g.nc + 1);
   DQ_RET(form_mid(ctx, g, 0, g.nn(), batch, g.Mid));
-  DQ_CLASS(ctx, kTInverse);
-  DQ_LAUNCH(ctx, launch_gj_cluster(g.Mid, g.nn(), g.A2, g.nn(), g.N, batch, g.logabs,
-                                   ctx->d_status, g.st));
+  DQ_CLASS(ctx, pair ? kTInversePair : kTInverse);
+  DQ_LAUNCH(ctx, launch_gj_cluster(g.Mid, g.nn(), g.A2, g.nn(), g.N, batch, pair ? nullptr : g.logabs,
+                                   ctx->d_status, g.st, pair));
   GemmArgs m = gemm0(g.N);
   m.A = g.LU; m.sA = g.nn(); m.tA = 1;
   m.ks = g.LD; m.sks = g.N; m.ks_mode = 2;
@@ -930,7 +932,7 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
   size_t off = 0;
   for (Group& g : ctx->g) {
     const int batch = g.C * (g.nc + 1);
-    DQ_RET(all_points_w1(ctx, g));
+    DQ_RET(all_points_w1(ctx, g, g.p.precision == DQMC_DF32));
     // G(c,0)^T = T_R^T Ds_R W1^T  and  W2 = T_L^T Ds_L Mid^{-1}, Y = W2 Db_R^{-1} U_R^T
     GemmArgs m = gemm0(g.N);
     m.A = g.RT; m.sA = g.nn(); m.tA = 1;
@@ -1000,7 +1002,7 @@ int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda, double* lo
   int off = 0;
   for (Group& g : ctx->g) {
     const int batch = g.C * (g.nc + 1);
-    DQ_RET(all_points_w1(ctx, g));
+    DQ_RET(all_points_w1(ctx, g, false));
     // G at every stabilisation point: W1 Db_R^{-1} U_R^T
     GemmArgs m = gemm0(g.N);
     m.A = g.W1; m.sA = g.nn();

@@ -10,6 +10,7 @@
 // stabilisation behind Eq. (3) and G_ij(tau_l), Sec. 2).
 #include <cooperative_groups.h>
 
+#include <algorithm>
 #include <cfloat>
 
 #include "common.cuh"
@@ -179,6 +180,36 @@ __device__ __forceinline__ void reflect_owned(double* M, int n, int j, const int
         ln2[c[q]] = nl2;
       }
     }
+  }
+}
+
+// Element helpers of the Gauss-Jordan kernel for FP64 and float pairs.
+__device__ __forceinline__ float gj_mag(double x) { return static_cast<float>(absd(x)); }
+__device__ __forceinline__ float gj_mag(df32 x) { return fabsf(x.hi); }
+__device__ __forceinline__ double gj_d(double x) { return x; }
+__device__ __forceinline__ double gj_d(df32 x) { return static_cast<double>(x); }
+__device__ __forceinline__ double gj_shfl(double x, int l) { return __shfl_sync(0xFFFFFFFFu, x, l); }
+__device__ __forceinline__ df32 gj_shfl(df32 x, int l) {
+  return df32(__shfl_sync(0xFFFFFFFFu, x.hi, l), __shfl_sync(0xFFFFFFFFu, x.lo, l));
+}
+// a b + c: for float pairs the product's error terms and one TwoSum with
+// c.hi, rounded once (about 15 FP32 instructions, relative error ~2^-48)
+__device__ __forceinline__ double gj_fma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ df32 gj_fma(df32 a, df32 b, df32 c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const df32 s = df_two_sum(c.hi, p);
+  return df_fast_two_sum(s.hi, s.lo + (c.lo + e));
+}
+
+// In-place FP64 -> float pair of a batch of matrices (same 8 bytes per entry).
+__global__ void __launch_bounds__(256) k_to_pair(double* A, long long count) {
+  for (long long e = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; e < count;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const double x = A[e];
+    reinterpret_cast<df32*>(A)[e] = df32(x);
   }
 }
 
@@ -363,20 +394,20 @@ __global__ void __launch_bounds__(512) k_qrp_cluster(double* Xall, long long sX,
 // rows and publishes it to every CTA of the cluster (distributed shared
 // memory, buffered by step parity), before the barrier.
 // ---------------------------------------------------------------------------
-template <int CS>
-__global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, double* Iall,
+template <int CS, typename T>
+__global__ void __launch_bounds__(512) k_gj_cluster(T* Aall, long long sA, double* Iall,
                                                    long long sI, int n, double* logabs,
                                                    int* status) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = static_cast<int>(cl.block_rank());
   const int b = blockIdx.x / CS;
-  double* A = Aall + b * sA;
+  T* A = Aall + b * sA;
   double* Ainv = Iall + b * sI;
-  __shared__ double prow[kMaxN], pend[kMaxN];
+  __shared__ T prow[kMaxN], pend[kMaxN];
   __shared__ int pr[kMaxN], ip[kMaxN];
   __shared__ unsigned char used[kMaxN];
   __shared__ AM cand[2][CS];  // best unused owned row of every CTA for the next column
-  __shared__ double sinv;
+  __shared__ T sinv;
   __shared__ double pivs[kMaxN];  // |pivot| of every step (log|det A| after the loop)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = threadIdx.x; i < n; i += blockDim.x) used[i] = 0;
@@ -386,7 +417,7 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
   auto publish = [&](int col, int slot) {
     AM m{-1.0f, n};
     for (int i = rank + CS * lane; i < n; i += CS * 32)
-      if (!used[i]) m = am_combine(m, AM{static_cast<float>(absd(A[static_cast<size_t>(i) * n + col])), i});
+      if (!used[i]) m = am_combine(m, AM{gj_mag(A[static_cast<size_t>(i) * n + col]), i});
     m = warp_am(m);
     if (lane < CS) *cl.map_shared_rank(&cand[slot][rank], lane) = m;
   };
@@ -408,16 +439,16 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
       while (p < n - 1 && used[p]) ++p;
     }
     if (threadIdx.x == 0) {  // pivot scalars: one thread, then broadcast
-      double piv = A[static_cast<size_t>(p) * n + k];
+      double piv = gj_d(A[static_cast<size_t>(p) * n + k]);
       if (!(absd(piv) > 0.0)) {
         atomicExch(status, kDevSingular);
         piv = DBL_MIN;
       }
       pivs[k] = absd(piv);
-      sinv = 1.0 / piv;
+      sinv = T(1.0 / piv);  // a float pair takes the FP64 reciprocal, split
     }
     __syncthreads();
-    const double ipiv = sinv;
+    const T ipiv = sinv;
     for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
       prow[jj] = (jj == k) ? ipiv : A[static_cast<size_t>(p) * n + jj] * ipiv;
     __syncthreads();
@@ -431,34 +462,34 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
     for (int i0 = rank + CS * w; i0 < n; i0 += 2 * CS * nw) {
       // two owned rows per warp and iteration, all their loads issued together
       const int ii[2] = {i0, i0 + CS * nw};
-      double xv[2][kRPL];
+      T xv[2][kRPL];
 #pragma unroll
       for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int t = 0; t < kRPL; ++t) {
           const int jj = lane + 32 * t;
-          xv[h][t] = (ii[h] < n && jj < n) ? A[static_cast<size_t>(ii[h]) * n + jj] : 0.0;
+          xv[h][t] = (ii[h] < n && jj < n) ? A[static_cast<size_t>(ii[h]) * n + jj] : T(0.0f);
         }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int i = ii[h];
         if (i >= n) continue;
-        double* Ai = A + static_cast<size_t>(i) * n;
+        T* Ai = A + static_cast<size_t>(i) * n;
         if (i == p) {
           for (int jj = lane; jj < n; jj += 32) pend[jj] = prow[jj];
           continue;
         }
-        double fk = 0.0;
+        T fk = T(0.0f);
 #pragma unroll
         for (int t = 0; t < kRPL; ++t)
           if (t == tk) fk = xv[h][t];
-        const double nf = -__shfl_sync(0xFFFFFFFFu, fk, lk);
-        const double vk = nf * prow[k];  // new entry of the pivot column (one product per row)
+        const T nf = -gj_shfl(fk, lk);
+        const T vk = nf * prow[k];  // new entry of the pivot column (one product per row)
 #pragma unroll
         for (int t = 0; t < kRPL; ++t) {
           const int jj = lane + 32 * t;
           if (jj < n) {
-            const double v = fma(nf, prow[jj], xv[h][t]);
+            const T v = gj_fma(nf, prow[jj], xv[h][t]);
             Ai[jj] = (jj == k) ? vk : v;
           }
         }
@@ -476,9 +507,9 @@ __global__ void __launch_bounds__(512) k_gj_cluster(double* Aall, long long sA, 
   for (int k = threadIdx.x; k < n; k += blockDim.x) ip[pr[k]] = k;
   cl.sync();
   for (int k = rank; k < n; k += CS) {
-    const double* Zr = A + static_cast<size_t>(pr[k]) * n;
+    const T* Zr = A + static_cast<size_t>(pr[k]) * n;
     for (int jj = threadIdx.x; jj < n; jj += blockDim.x)
-      Ainv[static_cast<size_t>(k) * n + jj] = Zr[ip[jj]];
+      Ainv[static_cast<size_t>(k) * n + jj] = gj_d(Zr[ip[jj]]);
   }
   if (logabs && rank == 0) {  // log|det| = sum_k log|pivot_k|, off the step loop
     double la = 0.0;
@@ -520,7 +551,7 @@ cudaError_t launch_qrp_cluster(double* Xt, long long sX, double* Qt, long long s
 }
 
 cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long sI, int n, int batch,
-                              double* logabs, int* status, cudaStream_t st) {
+                              double* logabs, int* status, cudaStream_t st, bool pair) {
   // Small batches (the per-point recompute: one matrix per chain) spread each
   // matrix over 4 CTAs, two of which fit on an SM (512 threads x 64
   // registers), so that twice as many warps hide the step latency; large
@@ -532,9 +563,17 @@ cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long s
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
       nsm = 1;
   }
+  if (pair) {  // float-pair elimination: A becomes an array of pairs in place
+    const long long count = static_cast<long long>(batch - 1) * sA + static_cast<long long>(n) * n;
+    k_to_pair<<<static_cast<int>(std::min<long long>((count + 255) / 256, 4096)), 256, 0, st>>>(A, count);
+    df32* Ap = reinterpret_cast<df32*>(A);
+    if (4LL * batch <= 2LL * nsm)
+      return launch_cluster(k_gj_cluster<4, df32>, 4, batch, st, Ap, sA, Ainv, sI, n, logabs, status);
+    return launch_cluster(k_gj_cluster<2, df32>, 2, batch, st, Ap, sA, Ainv, sI, n, logabs, status);
+  }
   if (4LL * batch <= 2LL * nsm)
-    return launch_cluster(k_gj_cluster<4>, 4, batch, st, A, sA, Ainv, sI, n, logabs, status);
-  return launch_cluster(k_gj_cluster<2>, 2, batch, st, A, sA, Ainv, sI, n, logabs, status);
+    return launch_cluster(k_gj_cluster<4, double>, 4, batch, st, A, sA, Ainv, sI, n, logabs, status);
+  return launch_cluster(k_gj_cluster<2, double>, 2, batch, st, A, sA, Ainv, sI, n, logabs, status);
 }
 
 }  // namespace dqmc

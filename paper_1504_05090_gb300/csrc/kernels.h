@@ -107,8 +107,10 @@ cudaError_t launch_qrp_cluster(double* Xt, long long sX, double* Qt, long long s
                                long long sD, double* Rtil, long long sR, double* vnorm, int n,
                                int batch, int* status, cudaStream_t st);
 // Gauss-Jordan: A (overwritten) -> Ainv, out of place; logabs may be null.
+// pair: eliminate in float pairs (A is converted in place first; Ainv and
+// logabs stay FP64).
 cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long sI, int n, int batch,
-                              double* logabs, int* status, cudaStream_t st);
+                              double* logabs, int* status, cudaStream_t st, bool pair = false);
 cudaError_t launch_set_identity(double* M, long long sM, double* D, long long sD, int n, int batch,
                                 cudaStream_t st);
 template <typename T>
