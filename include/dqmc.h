@@ -147,6 +147,21 @@ int dqmc_recompute_G(dqmc_ctx* ctx, double* max_drift_out);
  * dqmc_set_field and dqmc_recompute_G). */
 int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device);
 
+/* Time-origin averaged G_k(tau): the mean over n_origins origins
+ * tau_0 = s dtau, s = (o L_g) / n_origins (integer division, o < n_origins),
+ * of G_k(tau_0 + tau_l, tau_0), in the layout of dqmc_measure_Gtau.  Each
+ * origin is evaluated as G(tau) of the field rotated cyclically by s slices
+ * (slice l of the rotated field is slice l + s mod L of the chain's), whose
+ * weight in Eq. (3) is the same; the paper does not state this estimator.
+ * n_origins = 1 is dqmc_measure_Gtau.  Each further origin costs a rebuild of
+ * both UDV stacks and one G(tau) pass; afterwards every chain has its own
+ * field again, with rebuilt stacks and the working G replaced by the freshly
+ * stabilised G(0) (as dqmc_recompute_G, no drift recorded).  Requires
+ * 1 <= n_origins <= L of every group; allocates and frees a field copy and,
+ * for host output, one accumulator per group.  Synchronises.  Errors:
+ * DQMC_ERR_ARG, DQMC_ERR_OOM, DQMC_ERR_CUDA. */
+int dqmc_measure_Gtau_origins(dqmc_ctx* ctx, int n_origins, double* out, int out_on_device);
+
 /* dtau -> 0 extrapolation of G_k(tau) (Sec. 3, Fig. 2): runs at different
  * Trotter steps, each on its own grid tau_l = l dtau[r], are averaged over
  * their chains, put on the common fine grid tau_m = m beta / M (m = 0..M) by

@@ -68,6 +68,9 @@ points the paper leaves open:
       sign of G would leave Sigma = 2 i w_n or -2 eps_k there.  mu = 0 (half
       filling with the (n - 1/2) form of Eq. 1).  The quasi-continuous G(tau)
       between samples is the not-a-knot cubic spline of R15.
+  R17 time-origin averaging of G(tau) (an estimator, not stated in the
+      paper): the mean of G(tau_0 + tau, tau_0) over origins tau_0 on the
+      slice grid, each evaluated as G(tau) of the cyclically rotated field.
 """
 from __future__ import annotations
 
@@ -571,6 +574,19 @@ class Chain:
             for l, X in enumerate(self.gtau_matrices(sg)):
                 acc[l] += 0.5 * momentum_diag(X, p.Lx, p.Ly)
         return acc
+
+    def gtau_origins(self, n_origins):
+        """Time-origin average of G_k(tau) (reading R17): the mean over the
+        origins tau_0 = s dtau, s = (o L) // n_origins (o < n_origins), of
+        G_k(tau_0 + tau, tau_0).  By the cyclic invariance of the trace in
+        Eq. (3) that is G_k(tau) of the field rotated by s slices, whose slice
+        l is slice l + s (mod L) of this one; its weight is the same."""
+        p = self.p
+        acc = np.zeros((p.L + 1, p.N))
+        for o in range(n_origins):
+            s = (o * p.L) // n_origins
+            acc += Chain(p, field=np.roll(self.field, -s, axis=0)).gtau()
+        return acc / n_origins
 
     # -- derivatives of log W = log|det M_up| + log|det M_dn| ---------------
     def logw(self):

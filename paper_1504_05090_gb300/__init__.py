@@ -202,6 +202,21 @@ class DQMC:
         _lib.check(lib().dqmc_measure_Gtau(self._h, _ptr(host), 0), "dqmc_measure_Gtau", lib())
         return self._split(host, lambda g: (g.n_chains, g.L + 1, g.N))
 
+    def gtau_origins(self, n_origins, out=None):
+        """Time-origin averaged G_k(tau) (see dqmc_measure_Gtau_origins), in
+        the layout of gtau(); with `out` (a CUDA float64 tensor of
+        dqmc_gtau_size elements) the result stays on the device."""
+        n = int(lib().dqmc_gtau_size(self._h))
+        if out is not None:
+            assert out.is_cuda and out.numel() == n
+            _lib.check(lib().dqmc_measure_Gtau_origins(self._h, int(n_origins), _ptr(out), 1),
+                       "dqmc_measure_Gtau_origins", lib())
+            return out
+        host = np.empty(n)
+        _lib.check(lib().dqmc_measure_Gtau_origins(self._h, int(n_origins), _ptr(host), 0),
+                   "dqmc_measure_Gtau_origins", lib())
+        return self._split(host, lambda g: (g.n_chains, g.L + 1, g.N))
+
     def grad(self):
         """(dlogW/dt, dlogW/dlambda, logW) per chain, host arrays."""
         dt = np.empty(self.n_chains)

@@ -40,6 +40,8 @@ SIGNATURES = {
     "dqmc_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "dqmc_recompute_G": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dqmc_measure_Gtau": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "dqmc_measure_Gtau_origins": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                                 ctypes.c_int]),
     "dqmc_gtau_size": (ctypes.c_int64, [ctypes.c_void_p]),
     "dqmc_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                  ctypes.c_void_p, ctypes.c_int]),

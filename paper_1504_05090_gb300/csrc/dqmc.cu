@@ -31,6 +31,26 @@ __global__ void k_zero(double* p, long long n) {
     p[e] = 0.0;
 }
 
+// acc += a x
+__global__ void k_axpy(double* acc, const double* x, double a, long long n) {
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x)
+    acc[e] += a * x[e];
+}
+
+// Field rotated by s slices: out[c][l][i] = in[c][(l + s) mod L][i].
+__global__ void k_rotate_field(const int8_t* in, int8_t* out, int C, int L, int N, int s) {
+  const long long n = static_cast<long long>(C) * L * N;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long c = e / (static_cast<long long>(L) * N);
+    const long long r = e - c * L * N;
+    const int l = static_cast<int>(r / N), i = static_cast<int>(r - static_cast<long long>(l) * N);
+    const int ls = (l + s) % L;
+    out[e] = in[(c * L + ls) * N + i];
+  }
+}
+
 // log W = 2 (sum log Db_L(0) + log|det Mid(0)|) - lambda sum_il s_il   (det M_dn = e^{-lambda sum s} det M_up)
 __global__ void k_logw(const double* LD0, long long sLD, const double* logabs_mid, long long sMid,
                        const int8_t* field, int L, int N, double lam, double* out) {
@@ -927,10 +947,10 @@ int64_t dqmc_gtau_size(const dqmc_ctx* ctx) {
   return s;
 }
 
-int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
-  if (!ctx || !out) return DQMC_ERR_ARG;
-  size_t off = 0;
-  for (Group& g : ctx->g) {
+// G_k(tau_l) of every chain of group g, from its current stacks, into the
+// device array dst [C][L+1][N].
+int measure_gtau_group(dqmc_ctx* ctx, Group& g, double* dst) {
+  {
     const int batch = g.C * (g.nc + 1);
     DQ_RET(all_points_w1(ctx, g, g.p.precision == DQMC_DF32));
     // G(c,0)^T = T_R^T Ds_R W1^T  and  W2 = T_L^T Ds_L Mid^{-1}, Y = W2 Db_R^{-1} U_R^T
@@ -981,19 +1001,89 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
     ga.kind = kBIT; ga.vec_is_col = 0; ga.bin_slot = 1;
     DQ_CLASS(ctx, kTGtauProp);
     DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, pair, g.st));
+    DQ_CLASS(ctx, kTGtauFinal);
+    DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, dst, g.C, g.L, g.p.Lx, g.p.Ly, g.st));
+  }
+  return DQMC_OK;
+}
+
+int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device) {
+  if (!ctx || !out) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (Group& g : ctx->g) {
     const size_t cnt = static_cast<size_t>(g.C) * (g.L + 1) * g.N;
     if (out_on_device) {
-      DQ_CLASS(ctx, kTGtauFinal);
-      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, out + off, g.C, g.L, g.p.Lx, g.p.Ly, g.st));
+      DQ_RET(measure_gtau_group(ctx, g, out + off));
     } else {
-      DQ_CLASS(ctx, kTGtauFinal);
-      DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, g.gout, g.C, g.L, g.p.Lx, g.p.Ly, g.st));
+      DQ_RET(measure_gtau_group(ctx, g, g.gout));
       DQ_CK(cudaMemcpyAsync(out + off, g.gout, cnt * sizeof(double), cudaMemcpyDeviceToHost, g.st));
     }
     off += cnt;
   }
   if (!out_on_device) return check_status(ctx);
   return DQMC_OK;
+}
+
+int dqmc_measure_Gtau_origins(dqmc_ctx* ctx, int n_origins, double* out, int out_on_device) {
+  if (!ctx || !out || n_origins < 1) return DQMC_ERR_ARG;
+  for (const Group& g : ctx->g)
+    if (n_origins > g.L) return DQMC_ERR_ARG;
+  size_t off = 0;
+  for (Group& g : ctx->g) {
+    const size_t cnt = static_cast<size_t>(g.C) * (g.L + 1) * g.N;
+    const long long nf = static_cast<long long>(g.C) * g.L * g.N;
+    int8_t* saved = nullptr;
+    double* acc = nullptr;
+    if (cudaMalloc(&saved, nf) != cudaSuccess ||
+        (!out_on_device && cudaMalloc(&acc, cnt * sizeof(double)) != cudaSuccess)) {
+      cudaGetLastError();
+      if (saved) cudaFree(saved);
+      return DQMC_ERR_OOM;
+    }
+    if (out_on_device) acc = out + off;
+    const int blocks = static_cast<int>(std::min<long long>((static_cast<long long>(cnt) + 255) / 256, 1024));
+    int rc = DQMC_OK;
+    auto run = [&]() -> int {
+      DQ_CK(cudaMemcpyAsync(saved, g.field, nf, cudaMemcpyDeviceToDevice, g.st));
+      DQ_CLASS(ctx, kTMisc);
+      DQ_LAUNCH(ctx, (k_zero<<<blocks, 256, 0, g.st>>>(acc, static_cast<long long>(cnt)),
+                      cudaGetLastError()));
+      bool rotated = false;
+      for (int o = 0; o < n_origins; ++o) {
+        const int s = static_cast<int>((static_cast<long long>(o) * g.L) / n_origins);
+        if (s != 0) {  // the field rotated by s slices, and its stacks
+          DQ_CLASS(ctx, kTMisc);
+          DQ_LAUNCH(ctx, (k_rotate_field<<<static_cast<int>(std::min<long long>((nf + 255) / 256, 1024)),
+                                           256, 0, g.st>>>(saved, g.field, g.C, g.L, g.N, s),
+                          cudaGetLastError()));
+          DQ_RET(rebuild(ctx, g));
+          rotated = true;
+        }
+        DQ_RET(measure_gtau_group(ctx, g, g.gout));
+        DQ_CLASS(ctx, kTMisc);
+        DQ_LAUNCH(ctx, (k_axpy<<<blocks, 256, 0, g.st>>>(acc, g.gout, 1.0 / n_origins,
+                                                           static_cast<long long>(cnt)),
+                        cudaGetLastError()));
+      }
+      if (rotated) {  // the chain's own field and freshly stabilised stacks and G
+        DQ_CK(cudaMemcpyAsync(g.field, saved, nf, cudaMemcpyDeviceToDevice, g.st));
+        DQ_RET(rebuild(ctx, g));
+        DQ_RET(load_working(ctx, g));
+      }
+      if (!out_on_device)
+        DQ_CK(cudaMemcpyAsync(out + off, acc, cnt * sizeof(double), cudaMemcpyDeviceToHost, g.st));
+      DQ_CK(cudaStreamSynchronize(g.st));
+      return DQMC_OK;
+    };
+    rc = run();
+    if (rc != DQMC_OK)  // best effort: give the chains their own field back
+      cudaMemcpy(g.field, saved, nf, cudaMemcpyDeviceToDevice);
+    cudaFree(saved);
+    if (!out_on_device) cudaFree(acc);
+    if (rc != DQMC_OK) return rc;
+    off += cnt;
+  }
+  return check_status(ctx);
 }
 
 int dqmc_grad(dqmc_ctx* ctx, double* dlogW_dt, double* dlogW_dlambda, double* logW,

@@ -118,3 +118,11 @@ def test_matsubara_sigma_argument_checks_without_gpu(libpath):
     assert call(beta=0.0) == -1
     assert call(nf=0) == -1
     assert call(t=float("nan")) == -1
+
+
+def test_gtau_origins_argument_checks_without_gpu(libpath):
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    import numpy as np
+    buf = np.zeros(4)
+    assert lib.dqmc_measure_Gtau_origins(None, 2, buf.ctypes.data_as(ctypes.c_void_p), 0) == -1

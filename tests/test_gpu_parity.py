@@ -246,6 +246,32 @@ def test_gtau_matches_oracle(Lx, Ly, beta, dtau, ns):
             np.testing.assert_allclose(gt[c], ref, atol=1e-10 * np.max(np.abs(ref)))
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("df32", 1e-9)])
+def test_gtau_origin_average_matches_oracle(prec, tol):
+    """Time-origin averaged G(tau) over 3 origins (L = 16: s = 0, 5, 10)
+    against the oracle's average over rotated fields; afterwards the chains
+    hold their own field and continue exactly as the oracle's chains."""
+    g = _grp(4, 4, beta=2.0, dtau=0.125, ns=4, C=2, prec=prec)
+    p = _params(g)
+    with _sim([g], seed=23) as sim:
+        chains = [o.Chain(p, seed=23, chain=c) for c in range(2)]
+        sim.sweep(1)
+        for ch in chains:
+            ch.sweep()
+        f = sim.field()[0].copy()
+        ga = sim.gtau_origins(3)[0]
+        assert np.array_equal(sim.field()[0], f)
+        for c, ch in enumerate(chains):
+            ref = ch.gtau_origins(3)
+            np.testing.assert_allclose(ga[c], ref, rtol=0, atol=tol * np.max(np.abs(ref)))
+        np.testing.assert_allclose(sim.gtau_origins(1)[0], sim.gtau()[0], rtol=0, atol=1e-13)
+        sim.sweep(1)
+        for c, ch in enumerate(chains):
+            out = ch.sweep()
+            assert np.array_equal(sim.field()[0][c], ch.field)
+            assert _rel(sim.G(c, 0), out["G_up"]) < (GTOL if prec == "fp64" else 1e-8)
+
+
 def test_gtau_float_pair_propagation_matches_fp64():
     """Groups with float-pair working precision propagate G(l,0) and Y between
     stabilisation points in float pairs; on the same fields the spin-averaged

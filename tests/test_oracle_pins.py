@@ -646,3 +646,51 @@ def test_matsubara_sigma_2x2_hubbard_vs_lehmann():
     np.testing.assert_allclose(sigma, sig_ex, rtol=0, atol=1e-6)
     assert np.max(np.abs(sig_ex)) > 0.05                 # the interaction is visible
     assert np.max(np.abs(sigma[:, 1].real)) < 1e-9       # k = (pi, 0)
+
+
+# --------------------------------------------------------------------------
+# Time-origin averaged G(tau).
+# --------------------------------------------------------------------------
+def test_gtau_origin_rotation_is_the_shifted_unequal_time_green():
+    """For one field at small beta (no stabilisation needed), G(tau) of the
+    field rotated by s slices equals the direct product
+    B_{l+s} ... B_{s+1} (I + B_s ... B_1 B_L ... B_{s+1})^{-1}, slices mod L,
+    i.e. G(tau_s + tau_l, tau_s) of the original field."""
+    p = o.Params(2, 2, 0.25, 2.0, 1.0, 0.25, n_s=2)
+    rng = np.random.default_rng(9)
+    field = rng.choice([-1, 1], size=(p.L, p.N)).astype(np.int8)
+    ch = o.Chain(p, field=field)
+    s = 1
+    rot = o.Chain(p, field=np.roll(field, -s, axis=0))
+    got = rot.gtau()
+    B = lambda m, sg: ch.B((m - 1) % p.L + 1, sg)
+    ref = np.zeros((p.L + 1, p.N))
+    for sg in (1, -1):
+        A = np.eye(p.N)
+        for m in range(s + 1, s + p.L + 1):
+            A = B(m, sg) @ A                       # B_{s+L} ... B_{s+1}
+        G0 = np.linalg.inv(np.eye(p.N) + A)
+        X = G0
+        for l in range(p.L + 1):
+            if l > 0:
+                X = B(s + l, sg) @ X
+            ref[l] += 0.5 * o.momentum_diag(X, p.Lx, p.Ly)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+    # and the average with one origin is the plain estimator
+    np.testing.assert_array_equal(ch.gtau_origins(1), ch.gtau())
+
+
+def test_gtau_origin_average_is_unbiased_by_enumeration(tiny):
+    """Rotating the field is a weight-preserving bijection of the fields, so
+    the weighted mean of the origin-averaged estimator over all fields equals
+    the exact Fock-space G_k(tau) of the plain estimator."""
+    p, fields, w, _, F = tiny
+    avg = np.zeros((p.L + 1, p.N))
+    for f in range(len(w)):
+        avg += w[f] * o.Chain(p, field=fields[f]).gtau_origins(3)
+    avg /= w.sum()
+    exact = np.zeros((p.L + 1, p.N))
+    for l in range(p.L + 1):
+        G = F.gtau_up(l)
+        exact[l] = o.momentum_diag(G, p.Lx, p.Ly)   # spin down gives the same G_k at U > 0 half filling
+    np.testing.assert_allclose(avg, exact, rtol=0, atol=1e-11)
