@@ -526,6 +526,36 @@ def time_matsubara(pkg, torch, fine, g, beta, reps, n_freq=200):
                          "peak_source": "derived FP64 pipe: 152 SMs x 2 FMA/clk x 2 x 2070 MHz"}}
 
 
+def run_origins(args):
+    """Time-origin averaged G(tau) on the headline workload: device time of
+    one dqmc_measure_Gtau_origins call with 1 and with args.origins origins,
+    after warm-up sweeps.  Each extra origin is one rotation of the field,
+    a rebuild of both stacks and a G(tau) pass (the kernels of the sweep)."""
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    sim = make_sim(pkg, "df32", rank_seed(0))
+    gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        sim.sweep(1, measure=True)
+    res = {}
+    for n in (1, args.origins):
+        ms = []
+        for _ in range(max(3, args.steps)):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.gtau_origins(n, out=gbuf)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[n] = sorted(ms)[len(ms) // 2]
+    sim.close()
+    n = args.origins
+    print(json.dumps({"leg": "gtau_origins", "workload": WORKLOAD, "origins": n,
+                      "ms_one_origin": res[1], "ms_origins": res[n],
+                      "ms_per_extra_origin": (res[n] - res[1]) / max(1, n - 1)}), flush=True)
+
+
 def run_trotter(args):
     """The dtau -> 0 extrapolation alone, on seeded synthetic runs shaped like
     the 8x8 three-dtau configuration (256 chains per run, G_k(tau) on L + 1 =
@@ -652,6 +682,8 @@ def main():
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
     ap.add_argument("--scan-ns", action="store_true",
                     help="print the G drift against the stabilisation interval and exit")
+    ap.add_argument("--origins", type=int, default=0,
+                    help="time the time-origin averaged G(tau) with this many origins and exit")
     ap.add_argument("--trotter", action="store_true",
                     help="time the dtau -> 0 extrapolation of G_k(tau) alone and exit")
     args = ap.parse_args()
@@ -665,6 +697,8 @@ def main():
         run_scan_ns(args)
     elif args.trotter:
         run_trotter(args)
+    elif args.origins > 0:
+        run_origins(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
