@@ -51,12 +51,14 @@ def updates_per_sweep(chains):
 
 # ---------------------------------------------------------------------------
 # Several GPUs (torchrun, one rank per GPU): replicas only.  Every rank runs
-# the whole workload with its own seed (independent Markov chains, no data
-# exchange); the step time is the maximum over ranks and the value counts the
-# updates of all ranks (weak scaling).
+# the whole workload on its own chains: rank r holds the global chains
+# r C .. (r + 1) C - 1 of one seed (the chain id is the Philox counter word),
+# so N ranks sample exactly the chains of one N C-chain run, whatever the
+# split.  No data exchange; the step time is the maximum over ranks and the
+# value counts the updates of all ranks (weak scaling).
 # ---------------------------------------------------------------------------
-def rank_seed(rank):
-    return 1000 * rank
+def rank_chain_offset(rank):
+    return rank * W["chains"]
 
 
 def max_over_ranks(x, dist, device):
@@ -156,10 +158,10 @@ class Clocks:
 # ---------------------------------------------------------------------------
 # GPU arm.
 # ---------------------------------------------------------------------------
-def make_sim(pkg, precision, seed):
+def make_sim(pkg, precision, chain_offset):
     g = pkg.Group(Lx=W["Lx"], Ly=W["Ly"], t=W["t"], U=W["U"], beta=W["beta"], dtau=W["dtau"],
                   n_chains=W["chains"], stab_interval=W["ns"], delay_k=W["k"], precision=precision)
-    return pkg.DQMC([g], seed=seed)
+    return pkg.DQMC([g], seed=0, chain_offset=chain_offset)
 
 
 def step_device(sim, gbuf):
@@ -167,8 +169,8 @@ def step_device(sim, gbuf):
     sim.gtau(out=gbuf)
 
 
-def time_arm(pkg, torch, precision, steps, warmup, seed, dist):
-    sim = make_sim(pkg, precision, seed)
+def time_arm(pkg, torch, precision, steps, warmup, chain_offset, dist):
+    sim = make_sim(pkg, precision, chain_offset)
     gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
     for _ in range(warmup):
         step_device(sim, gbuf)
@@ -327,18 +329,18 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    seed = rank_seed(rank)  # independent chains per rank (weak scaling)
+    offset = rank_chain_offset(rank)  # this rank's global chains (weak scaling)
 
     # Mixed arm: float-pair (df32) Metropolis / delayed update / wrap on the FP32
     # pipe with FP64 stabilisation -- the same G drift as plain FP64 (see
     # --scan-ns).  Plain FP64 and FP32 working precision are timed beside it.
-    sim, gbuf, mixed = time_arm(pkg, torch, "df32", args.steps, args.warmup, seed, dist)
+    sim, gbuf, mixed = time_arm(pkg, torch, "df32", args.steps, args.warmup, offset, dist)
     prof = kernel_profile(sim, gbuf, args.steps, torch)
     e2e = e2e_arm(pkg, torch, sim, max(1, min(args.steps, 3)))
     sim.close()
     arms = {}
     for prec in ("fp64", "fp32"):
-        s2, b2, res = time_arm(pkg, torch, prec, args.steps, args.warmup, seed, dist)
+        s2, b2, res = time_arm(pkg, torch, prec, args.steps, args.warmup, offset, dist)
         res["kernel_ms_per_step"] = {k: v[0] / args.steps
                                      for k, v in kernel_profile(s2, b2, args.steps, torch).items()}
         s2.close()
@@ -533,7 +535,7 @@ def run_origins(args):
     a rebuild of both stacks and a G(tau) pass (the kernels of the sweep)."""
     import torch
     import paper_1504_05090_gb300 as pkg
-    sim = make_sim(pkg, "df32", rank_seed(0))
+    sim = make_sim(pkg, "df32", 0)
     gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
         sim.sweep(1, measure=True)

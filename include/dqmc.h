@@ -90,6 +90,16 @@ typedef struct dqmc_ctx dqmc_ctx; /* opaque, library-owned */
 int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed,
               void* stream, dqmc_ctx** out);
 
+/* As dqmc_init, with the chains numbered from chain_offset >= 0 in the
+ * Philox counter (initial field and proposals): a context holding chains
+ * chain_offset .. chain_offset + n - 1 draws exactly what those chains draw
+ * in a single context of all chains, so results do not depend on how the
+ * chains are split over contexts or GPUs.  Chain indices of the accessors
+ * stay local (0 .. n - 1).  chain_offset + n must not exceed 2^31 - 1.
+ * Errors as dqmc_init. */
+int dqmc_init_at(const dqmc_group* groups, int n_groups, uint64_t seed, int64_t chain_offset,
+                 void* stream, dqmc_ctx** out);
+
 /* Run n_sweeps >= 0 Monte Carlo sweeps of every chain (Sec. 2: the sum of
  * Eq. (3) sampled by Metropolis).  A sweep visits slices l = 1..L in order
  * and sites i = 0..N-1 within a slice; the flip of s[l][i] is accepted iff

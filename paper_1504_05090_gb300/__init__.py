@@ -73,7 +73,7 @@ class DQMC:
 
     All work is enqueued on the torch stream current at construction."""
 
-    def __init__(self, groups, seed=0, stream=None):
+    def __init__(self, groups, seed=0, stream=None, chain_offset=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("DQMC needs a CUDA device")
@@ -83,9 +83,10 @@ class DQMC:
         self.stream = stream
         arr = (_lib.DqmcGroup * len(self.groups))(*[g._c() for g in self.groups])
         h = ctypes.c_void_p()
-        _lib.check(lib().dqmc_init(arr, len(self.groups), int(seed) & 0xFFFFFFFFFFFFFFFF,
-                                   ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
-                   "dqmc_init", lib())
+        _lib.check(lib().dqmc_init_at(arr, len(self.groups), int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                      int(chain_offset), ctypes.c_void_p(stream.cuda_stream),
+                                      ctypes.byref(h)),
+                   "dqmc_init_at", lib())
         self._h = h
         self.n_chains = lib().dqmc_num_chains(h)
 

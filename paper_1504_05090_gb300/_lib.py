@@ -37,6 +37,8 @@ class DqmcGroup(ctypes.Structure):
 SIGNATURES = {
     "dqmc_init": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_int, ctypes.c_uint64,
                                  ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    "dqmc_init_at": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_int, ctypes.c_uint64,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
     "dqmc_sweep": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]),
     "dqmc_recompute_G": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dqmc_measure_Gtau": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),

@@ -145,6 +145,7 @@ struct dqmc_ctx {
   double tms[kTNumClasses] = {};
   long long tcount[kTNumClasses] = {};
   uint64_t seed = 0;
+  int64_t chain_offset = 0;  // global id of this context's first chain (Philox counter word)
   uint32_t* d_sweep = nullptr;
   int* d_status = nullptr;
   int total = 0;
@@ -484,7 +485,7 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
   ma.N = g.N;
   ma.L = g.L;
   ma.k = g.p.delay_k;
-  ma.chain0 = g.chain0;
+  ma.chain0 = static_cast<int>(g.chain0 + ctx->chain_offset);  // Philox chain word
   ma.key0 = static_cast<uint32_t>(ctx->seed);
   ma.key1 = static_cast<uint32_t>(ctx->seed >> 32);
   ma.sweep_ctr = ctx->d_sweep;
@@ -744,9 +745,19 @@ void dqmc_destroy(dqmc_ctx* ctx) {
 }
 
 int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* stream, dqmc_ctx** out) {
-  if (!groups || n_groups < 1 || !out) return DQMC_ERR_ARG;
+  return dqmc_init_at(groups, n_groups, seed, 0, stream, out);
+}
+
+int dqmc_init_at(const dqmc_group* groups, int n_groups, uint64_t seed, int64_t chain_offset,
+                 void* stream, dqmc_ctx** out) {
+  if (!groups || n_groups < 1 || !out || chain_offset < 0) return DQMC_ERR_ARG;
   *out = nullptr;
   for (int i = 0; i < n_groups; ++i) DQ_RET(validate(groups[i]));
+  {  // every chain id must fit the (signed) chain index of the kernels
+    int64_t total = chain_offset;
+    for (int i = 0; i < n_groups; ++i) total += groups[i].n_chains;
+    if (total > 0x7FFFFFFFLL) return DQMC_ERR_ARG;
+  }
   int dev = 0;
   cudaDeviceProp prop;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess ||
@@ -756,6 +767,7 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
   if (!ctx) return DQMC_ERR_OOM;
   ctx->st = static_cast<cudaStream_t>(stream);
   ctx->seed = seed;
+  ctx->chain_offset = chain_offset;
   ctx->nsm = prop.multiProcessorCount;
   ctx->g.resize(n_groups);
   int rc = dev_alloc(ctx, &ctx->d_sweep, sizeof(uint32_t));
@@ -775,7 +787,8 @@ int dqmc_init(const dqmc_group* groups, int n_groups, uint64_t seed, void* strea
     chain0 += g.C;
     if (rc == DQMC_OK) {
       ++ctx->launches;
-      const cudaError_t e = launch_init_field(g.field, g.C, g.L, g.N, g.chain0, seed, ctx->st);
+      const cudaError_t e = launch_init_field(g.field, g.C, g.L, g.N,
+                                              static_cast<int>(g.chain0 + chain_offset), seed, ctx->st);
       if (e != cudaSuccess) {
         g_last_cuda = e;
         g_last_line = __LINE__;

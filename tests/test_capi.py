@@ -126,3 +126,12 @@ def test_gtau_origins_argument_checks_without_gpu(libpath):
     import numpy as np
     buf = np.zeros(4)
     assert lib.dqmc_measure_Gtau_origins(None, 2, buf.ctypes.data_as(ctypes.c_void_p), 0) == -1
+
+
+def test_init_at_rejects_bad_chain_offsets_without_gpu(libpath):
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    h = ctypes.c_void_p()
+    g = _lib.DqmcGroup(4, 4, 0.25, 2.0, 2.0, 0.125, 2, 4, 4, 0)
+    assert lib.dqmc_init_at(ctypes.byref(g), 1, 0, -1, None, ctypes.byref(h)) == -1
+    assert lib.dqmc_init_at(ctypes.byref(g), 1, 0, 0x7FFFFFFF, None, ctypes.byref(h)) == -1

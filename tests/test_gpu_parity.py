@@ -453,3 +453,21 @@ def test_full_size_16x16_sampled_chains():
         np.testing.assert_allclose(spin[:, minus], spin, rtol=1e-12, atol=1e-14)
         # C(0) = <(S^z)^2> = (n - 2 docc) / 4 per site, from the separate observables
         np.testing.assert_allclose(spin[:, 0], (obs[:, 0] - 2.0 * obs[:, 1]) / 4.0, rtol=1e-12)
+
+
+def test_chain_offset_makes_results_independent_of_the_split():
+    """Four chains in one context equal chains 0-1 and 2-3 in two contexts
+    created with chain offsets 0 and 2: fields, G and accepted counts after
+    two sweeps are bit-identical (the Philox counter carries the global id)."""
+    import paper_1504_05090_gb300 as pkg
+    g4 = _grp(4, 4, beta=1.0, ns=3, k=4, C=4)
+    g2 = _grp(4, 4, beta=1.0, ns=3, k=4, C=2)
+    with _sim([g4], seed=31) as whole:
+        whole.sweep(2)
+        for half, off in ((0, 0), (1, 2)):
+            with pkg.DQMC([g2], seed=31, chain_offset=off) as part:
+                part.sweep(2)
+                assert np.array_equal(part.field()[0], whole.field()[0][off:off + 2])
+                for c in range(2):
+                    assert np.array_equal(part.G(c, 0), whole.G(off + c, 0))
+                assert np.array_equal(part.stats()[1], whole.stats()[1][off:off + 2])

@@ -1,9 +1,10 @@
 """Host logic of bench.py on several GPUs, exercised with two gloo ranks on CPU.
 
 bench.py under torchrun runs one replica of the workload per GPU (the chains
-are independent Markov chains: no data exchange).  Each rank seeds its own
-chains, the reported step time is the maximum over ranks and the value counts
-the updates of every rank.  No GPU is needed for any of this."""
+are independent Markov chains: no data exchange).  Each rank holds its own
+block of global chain ids, the reported step time is the maximum over ranks
+and the value counts the updates of every rank.  No GPU is needed for any of
+this."""
 import os
 import socket
 import sys
@@ -28,7 +29,7 @@ def _rank_main(rank, world, port, ms, q):
     try:
         import bench
         slow = bench.max_over_ranks(ms[rank], dist, "cpu")
-        q.put((rank, slow, bench.rank_seed(rank), bench.job_value(world, slow)))
+        q.put((rank, slow, bench.rank_chain_offset(rank), bench.job_value(world, slow)))
     finally:
         dist.destroy_process_group()
 
@@ -48,21 +49,24 @@ def test_two_ranks_report_the_slowest_rank_and_the_whole_job():
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, slow, seed, value in out:
+    for rank, slow, offset, value in out:
         assert slow == max(ms)  # every rank sees the slowest rank's time
         assert value == pytest.approx(2 * bench.updates_per_sweep(bench.W["chains"]) / 0.6555)
-    seeds = [o[2] for o in out]
-    assert len(set(seeds)) == 2
+    # the ranks' chain blocks tile 0 .. 2C - 1 without overlap
+    assert [o[2] for o in out] == [0, bench.W["chains"]]
 
 
 def test_ranks_sample_independent_chains():
-    """Different rank seeds give different initial fields for the same chain
-    index (the Philox key differs), so the replicas are independent."""
+    """Local chain 3 of rank 1 is global chain C + 3: its initial field (the
+    Philox counter carries the global id) differs from rank 0's chain 3, so
+    the replicas are independent, and equals the field that chain has in a
+    single run of 2C chains."""
     sys.path.insert(0, ROOT)
     import bench
     from oracle import dqmc as o
-    f0 = o.initial_field(bench.rank_seed(0), 3, 16, 8)
-    f1 = o.initial_field(bench.rank_seed(1), 3, 16, 8)
+    f0 = o.initial_field(0, bench.rank_chain_offset(0) + 3, 16, 8)
+    f1 = o.initial_field(0, bench.rank_chain_offset(1) + 3, 16, 8)
+    assert np.array_equal(f1, o.initial_field(0, bench.W["chains"] + 3, 16, 8))
     assert f0.shape == f1.shape
     assert not np.array_equal(f0, f1)
     # about half of the spins differ, as for independent fields
