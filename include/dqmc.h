@@ -2,7 +2,9 @@
  * dqmc.h -- C ABI of the GB300 BSS determinant quantum Monte Carlo library
  * (libdqmc.so) for the half-filled Hubbard model on periodic Lx x Ly square
  * clusters, after Rost & Bluemer, arXiv:1504.05090, Sec. 2 "Model and
- * Methods", Eqs. (1)-(3).
+ * Methods", Eqs. (1)-(3), with the analysis steps of Sec. 3 (dtau -> 0
+ * extrapolation of G_k(tau), Fig. 2; Matsubara transform and self-energy,
+ * Eqs. (5)-(6)) and Sec. 4 (real-space spin correlation, Fig. 5).
  *
  * Notation.  N = Lx*Ly sites, site i = x + Lx*y.  L = beta/dtau Trotter slices
  * (the paper's Lambda, Eq. (2)).  K is the hopping matrix of Eq. (1)
@@ -22,7 +24,9 @@
  *    dqmc_destroy().  Output buffers belong to the caller.
  *  - Work is enqueued on the CUDA stream given to dqmc_init (NULL = the legacy
  *    default stream).  Calls that write host memory synchronise that stream
- *    before returning; calls with out_on_device != 0 do not.
+ *    before returning; calls with out_on_device != 0 do not.  The stateless
+ *    analysis calls (dqmc_trotter_extrapolate, dqmc_matsubara_sigma) run on
+ *    the legacy default stream and always synchronise it.
  *  - Chains are numbered globally in group order: group 0's chains first.
  *    Arrays "per chain" are laid out in that order; a group's block of a
  *    per-chain array with a group-dependent row length (field, G(tau)) has the
