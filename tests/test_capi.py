@@ -135,3 +135,29 @@ def test_init_at_rejects_bad_chain_offsets_without_gpu(libpath):
     g = _lib.DqmcGroup(4, 4, 0.25, 2.0, 2.0, 0.125, 2, 4, 4, 0)
     assert lib.dqmc_init_at(ctypes.byref(g), 1, 0, -1, None, ctypes.byref(h)) == -1
     assert lib.dqmc_init_at(ctypes.byref(g), 1, 0, 0x7FFFFFFF, None, ctypes.byref(h)) == -1
+
+
+def test_every_timed_kernel_class_has_a_roofline_formula(libpath):
+    """bench.py turns the library's per-class device times into roofline
+    fractions; every class that does arithmetic needs a work formula there,
+    for every working precision (host logic, no GPU)."""
+    import sys
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    sys.path.insert(0, ROOT)
+    import bench
+    names = []
+    for c in range(64):
+        name = lib.dqmc_timing_class_name(c)
+        if not name:
+            break
+        names.append(name.decode())
+    assert "qr_pivot" in names and "gj_inverse_pair" in names
+    bookkeeping = {"gtau_finalize", "grad_terms", "misc"}
+    for prec in ("df32", "fp64", "fp32"):
+        for name in names:
+            bound, work = bench.class_work(name, 0.6, prec)
+            if name in bookkeeping:
+                assert bound is None
+            else:
+                assert bound in ("alu", "alu64", "alu32x2", "tensor") and work > 0, (name, prec)
