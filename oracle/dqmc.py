@@ -71,6 +71,12 @@ points the paper leaves open:
   R17 time-origin averaging of G(tau) (an estimator, not stated in the
       paper): the mean of G(tau_0 + tau, tau_0) over origins tau_0 on the
       slice grid, each evaluated as G(tau) of the cyclically rotated field.
+  R18 the correlation length of Sec. 4 (Fig. 5, "an exponential fit" to the
+      real-space spin correlation) is read as the least-squares line through
+      (|r|, ln((-1)^(dx+dy) C(r))) over 0 < |r| <= dmax, |r| the minimum-image
+      distance, points with a non-positive staggered value left out;
+      xi = -1/slope.  The paper names neither the form, the distance nor the
+      fitted range.
 """
 from __future__ import annotations
 
@@ -86,8 +92,8 @@ __all__ = [
     "adjacency", "dispersion", "exp_hopping", "hs_lambda", "hs_prefactor",
     "n_slices", "b_matrix", "b_inverse", "udv_chain", "green_from_udv",
     "two_stack_green", "Params", "Chain", "observables_from_g",
-    "spin_correlation_from_g", "momentum_diag", "weight_log", "trotter_extrapolate",
-    "matsubara_sigma",
+    "spin_correlation_from_g", "min_image_distance", "correlation_length",
+    "momentum_diag", "weight_log", "trotter_extrapolate", "matsubara_sigma",
 ]
 
 MASK32 = 0xFFFFFFFF
@@ -352,6 +358,52 @@ def spin_correlation_from_g(G_up, G_dn, Lx, Ly):
             du = nd[i] * nu[j]
             C[site_index(dx, dy, Lx)] = np.sum(0.25 * (uu + dd - ud - du)) / N
     return C
+
+
+def min_image_distance(Lx, Ly):
+    """|r| of every displacement r = dx + Lx dy on the periodic cluster, in the
+    minimum-image convention: sqrt(min(dx, Lx - dx)^2 + min(dy, Ly - dy)^2)."""
+    d = np.empty(Lx * Ly)
+    for dy in range(Ly):
+        for dx in range(Lx):
+            ax, ay = min(dx, Lx - dx), min(dy, Ly - dy)
+            d[site_index(dx, dy, Lx)] = math.sqrt(ax * ax + ay * ay)
+    return d
+
+
+def correlation_length(C, Lx, Ly, dmax=None):
+    """Spin correlation length xi of Sec. 4 (Fig. 5) from one real-space
+    C(r) (index dx + Lx dy, as spin_correlation_from_g), by the exponential fit
+    the paper names (reading R18; the paper gives neither the fitted form,
+    the distance nor the range):
+      * staggered magnitude c(r) = (-1)^(dx + dy) C(r), positive where the
+        correlations are antiferromagnetic, as at half filling;
+      * distance d(r) = min_image_distance;
+      * least squares, unweighted, of ln c(r) = a - d(r) / xi over every r
+        with 0 < d(r) <= dmax and c(r) > 0 (dmax = min(Lx, Ly) / 2 if None),
+        i.e. the straight line through the points (d, ln c):
+          b = (n S_dy - S_d S_y) / (n S_dd - S_d^2);
+    xi = -1 / b for b < 0, +inf for b >= 0 (no decay within the cluster), and
+    nan when the points have fewer than two distinct distances."""
+    C = np.asarray(C, dtype=np.float64)
+    if dmax is None:
+        dmax = 0.5 * min(Lx, Ly)
+    d = min_image_distance(Lx, Ly)
+    sgn = np.array([(-1.0) ** (i % Lx + i // Lx) for i in range(Lx * Ly)])
+    c = sgn * C
+    pts = [(d[r], math.log(c[r])) for r in range(Lx * Ly) if 0.0 < d[r] <= dmax and c[r] > 0.0]
+    n = len(pts)
+    if n < 2:
+        return float("nan")
+    sd = sum(p[0] for p in pts)
+    sy = sum(p[1] for p in pts)
+    sdd = sum(p[0] * p[0] for p in pts)
+    sdy = sum(p[0] * p[1] for p in pts)
+    den = n * sdd - sd * sd
+    if not den > 0.0:
+        return float("nan")
+    b = (n * sdy - sd * sy) / den
+    return -1.0 / b if b < 0.0 else float("inf")
 
 
 def momentum_diag(X, Lx, Ly):

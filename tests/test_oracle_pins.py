@@ -450,6 +450,46 @@ def test_t_gradient_expectation_is_hellmann_feynman():
     assert (w * g).sum() / w.sum() == pytest.approx((math.log(zp) - math.log(zm)) / (2 * h), rel=1e-7)
 
 
+def _docc_from_lambda_gradient(p, fields, w):
+    """Double occupancy from the field average of d log W / d lambda.  With
+    Z_dtau = C^{NL} sum_h W(h), d ln C/dU = -dtau/4 and (cosh lambda =
+    e^{dtau U/2}) d lambda/dU = (dtau/2) coth lambda, equating
+    d ln Z_dtau/dU = -beta sum_i <(n_up - 1/2)(n_dn - 1/2)> gives
+      d = <n>/2 - coth(lambda) <d log W/d lambda> / (2 N L)."""
+    dl = np.array([o.Chain(p, field=fields[f]).grad()[1] for f in range(len(w))])
+    return dl, (w * dl).sum() / w.sum()
+
+
+def test_lambda_gradient_expectation_is_double_occupancy(tiny):
+    """<d log W/d lambda> over all fields of the 2x2 cluster (L = 3) turns into
+    the exact Fock-space double occupancy through the relation above; a wrong
+    sign of sigma, a wrong slice of G or a dropped spin in the oracle's
+    lambda-gradient breaks it."""
+    p, fields, w, greens, F = tiny
+    _, mean = _docc_from_lambda_gradient(p, fields, w)
+    d = 0.5 - mean / math.tanh(p.lam) / (2 * p.N * p.L)
+    assert d == pytest.approx(F.docc(), rel=1e-11)
+
+
+def test_lambda_gradient_double_occupancy_away_from_half_filling():
+    """The same relation on the 3x2 cluster (L = 2, t = 1, U = 4, dtau = 0.5),
+    whose odd ring makes it non-bipartite, so <n> != 1: the <n>/2 term is
+    checked too."""
+    Lx, Ly, t, U, dtau, L = 3, 2, 1.0, 4.0, 0.5, 2
+    p = o.Params(Lx, Ly, t, U, L * dtau, dtau, n_s=2)
+    fields, w, Z, greens = en.enumerate_sum(p, want_g=True)
+    F = fock.FockHubbard(Lx, Ly, t, U, dtau, L)
+    n = np.array([o.observables_from_g(greens[1][f], greens[-1][f], p.K)[0]
+                  for f in range(len(w))])
+    n_mean = (w * n).sum() / w.sum()
+    n_fock = F.expect(np.diag(np.sum(F.nu + F.nd, axis=1))) / F.N
+    assert n_mean == pytest.approx(n_fock, rel=1e-11)
+    assert abs(n_mean - 1.0) > 1e-3  # the check below sees the <n> term
+    _, mean = _docc_from_lambda_gradient(p, fields, w)
+    d = 0.5 * n_mean - mean / math.tanh(p.lam) / (2 * p.N * p.L)
+    assert d == pytest.approx(F.docc(), rel=1e-11)
+
+
 # --------------------------------------------------------------------------
 # Monte Carlo statistics: the Markov chain samples Eq. (3).
 # --------------------------------------------------------------------------
@@ -694,3 +734,70 @@ def test_gtau_origin_average_is_unbiased_by_enumeration(tiny):
         G = F.gtau_up(l)
         exact[l] = o.momentum_diag(G, p.Lx, p.Ly)   # spin down gives the same G_k at U > 0 half filling
     np.testing.assert_allclose(avg, exact, rtol=0, atol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# Correlation length of Sec. 4 (Fig. 5): the exponential fit (reading R18).
+# --------------------------------------------------------------------------
+def _staggered_exponential(Lx, Ly, xi, amp):
+    """C(r) = amp (-1)^(dx+dy) e^{-|r|/xi}, |r| the minimum-image distance,
+    written out here from the coordinates (not from the oracle's helpers)."""
+    C = np.empty(Lx * Ly)
+    for dy in range(Ly):
+        for dx in range(Lx):
+            rx, ry = min(dx, Lx - dx), min(dy, Ly - dy)
+            C[dx + Lx * dy] = amp * (-1) ** (dx + dy) * math.exp(-math.hypot(rx, ry) / xi)
+    return C
+
+
+@pytest.mark.parametrize("Lx,Ly,xi,amp,dmax", [(8, 8, 1.7, 0.3, None), (16, 16, 3.7, 0.05, None),
+                                               (8, 6, 2.2, 1.0, 2.5), (16, 4, 0.9, 0.2, 8.0)])
+def test_correlation_length_recovers_an_exact_exponential(Lx, Ly, xi, amp, dmax):
+    """A staggered exponential returns its own xi (any amplitude, range, and
+    rectangular clusters, where mixing dx and dy or dropping the minimum
+    image shifts the distances and the fit)."""
+    C = _staggered_exponential(Lx, Ly, xi, amp)
+    assert o.correlation_length(C, Lx, Ly, dmax) == pytest.approx(xi, rel=1e-12)
+
+
+def test_correlation_length_skips_non_positive_staggered_values():
+    """Points whose staggered value is <= 0 (noise at long distance) carry no
+    logarithm and are left out; the rest still give the exact xi."""
+    Lx = Ly = 8
+    C = _staggered_exponential(Lx, Ly, 2.0, 0.25)
+    flip = [3 + Lx * 3, 4 + Lx * 4, 4 + Lx * 1]  # far points turned ferromagnetic
+    C[flip] *= -1.0
+    C[2 + Lx * 3] = 0.0
+    assert o.correlation_length(C, Lx, Ly) == pytest.approx(2.0, rel=1e-12)
+
+
+def test_correlation_length_degenerate_cases():
+    Lx = Ly = 8
+    # no decay: a constant staggered pattern has slope 0 -> infinite xi
+    C = _staggered_exponential(Lx, Ly, 1e300, 0.1)
+    assert o.correlation_length(C, Lx, Ly) == math.inf
+    # growing correlations -> infinite xi as well
+    assert o.correlation_length(-_staggered_exponential(Lx, Ly, -3.0, -0.1), Lx, Ly) == math.inf
+    # a single distance (only the nearest neighbours in range) -> nan
+    assert math.isnan(o.correlation_length(_staggered_exponential(Lx, Ly, 2.0, 1.0), Lx, Ly, 1.0))
+    # no positive staggered value at all -> nan
+    assert math.isnan(o.correlation_length(-_staggered_exponential(Lx, Ly, 2.0, 1.0), Lx, Ly))
+
+
+def test_correlation_length_is_the_least_squares_line():
+    """On noisy data the fit equals the slope of numpy's degree-1 polynomial
+    least squares through the same points, selected here independently."""
+    Lx, Ly = 12, 10
+    rng = np.random.default_rng(5)
+    C = _staggered_exponential(Lx, Ly, 2.5, 0.2) * np.exp(0.2 * rng.standard_normal(Lx * Ly))
+    dmax = 4.2
+    d, y = [], []
+    for dy in range(Ly):
+        for dx in range(Lx):
+            r = math.hypot(min(dx, Lx - dx), min(dy, Ly - dy))
+            c = (-1) ** (dx + dy) * C[dx + Lx * dy]
+            if 0 < r <= dmax and c > 0:
+                d.append(r)
+                y.append(math.log(c))
+    slope = np.polyfit(d, y, 1)[0]
+    assert o.correlation_length(C, Lx, Ly, dmax) == pytest.approx(-1.0 / slope, rel=1e-11)
