@@ -225,13 +225,31 @@ FP64_PEAK = 152 * 2 * 2 * 2.07e9 / 1e12
 DF32_PEAK = 2 * 152 * 128 * 2.07e9 / 14 / 1e12
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of the current kernel on the 64-chain 16x16 case, whose launches
-# do the same work as the benchmark's (one slice of 64 chains; 64 QRs of order
-# 256).  A kernel that changes after its capture drops out of this table.
-TRAFFIC = {
-    ("metropolis", "df32"): 33648128 + 7424,  # 64 x 512 KB of G read once
-    ("qr_pivot", None): 39098112 + 53863168,  # X read, Q^T and Rtil written
-}
+# ncu capture of a kernel on the 64-chain 16x16 case, whose launches do the same
+# work as the benchmark's (one slice of 64 chains; 64 QRs of order 256), keyed
+# by (class, precision).  Each entry names the source file of the kernel and
+# the SHA-256 prefix that file had when the counters were taken: if the file
+# has changed since, the entry is stale and the roofline line reports null.
+TRAFFIC = {}
+
+
+def _source_sha16(rel):
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_1504_05090_gb300", "csrc", rel), "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def traffic_bytes(cls, precision):
+    """Measured DRAM bytes per launch of the class's dominant kernel, or None
+    when there is no capture of the current source."""
+    ent = TRAFFIC.get((cls, precision), TRAFFIC.get((cls, None)))
+    if ent is None:
+        return None
+    nbytes, src, sha = ent
+    return nbytes if _source_sha16(src) == sha else None
 
 
 def class_work(cls, acceptance, precision):
@@ -286,7 +304,7 @@ def roofline(profile, steps, acceptance, precision="df32"):
             peak, src = DF32_PEAK, "derived df32: FP32 pipe 152 x 128 FMA/clk x 2 x 2070 MHz / 14 instr"
         else:
             peak, src = 2 * 152 * 128 * 2.07e9 / 1e12, "derived FP32 pipe: 152 x 128 FMA/clk x 2 x 2070 MHz"
-        traffic = TRAFFIC.get((cls, precision), TRAFFIC.get((cls, None)))
+        traffic = traffic_bytes(cls, precision)
         rows[cls] = {"bound": "tensor" if bound == "tensor" else "alu", "kernel": cls,
                      "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                      "traffic": traffic, "peak_source": src,

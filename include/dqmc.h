@@ -173,7 +173,9 @@ int dqmc_measure_Gtau(dqmc_ctx* ctx, double* out, int out_on_device);
  * stabilised G(0) (as dqmc_recompute_G, no drift recorded).  Requires
  * 1 <= n_origins <= L of every group; allocates and frees a field copy and,
  * for host output, one accumulator per group.  Synchronises.  Errors:
- * DQMC_ERR_ARG, DQMC_ERR_OOM, DQMC_ERR_CUDA. */
+ * DQMC_ERR_ARG, DQMC_ERR_OOM, DQMC_ERR_CUDA.  After an error the call tries
+ * to restore every chain's own field and to rebuild its stacks and G; if that
+ * fails as well, call dqmc_recompute_G before sweeping again. */
 int dqmc_measure_Gtau_origins(dqmc_ctx* ctx, int n_origins, double* out, int out_on_device);
 
 /* dtau -> 0 extrapolation of G_k(tau) (Sec. 3, Fig. 2): runs at different
@@ -270,6 +272,25 @@ int dqmc_reset_observables(dqmc_ctx* ctx);
 int64_t dqmc_spin_correlation_size(const dqmc_ctx* ctx);
 int dqmc_get_spin_correlation(const dqmc_ctx* ctx, double* out);
 
+/* Spin correlation length of Sec. 4 (Fig. 5, "an exponential fit" to the
+ * real-space spin correlation), from the C(r) accumulated by the sweeps (see
+ * dqmc_get_spin_correlation) divided by the number of measurements.  The
+ * paper states neither the fitted form nor the range; the reading taken is
+ * the least-squares line through the points (|r|, ln c(r)) with
+ *   c(r) = (-1)^(dx+dy) C(r)        (staggered: > 0 for antiferromagnetic order)
+ *   |r|  = sqrt(min(dx,Lx-dx)^2 + min(dy,Ly-dy)^2)   (minimum image)
+ * over every displacement with 0 < |r| <= dmax and c(r) > 0, and
+ * xi = -1/slope; +inf if the slope is >= 0 (no decay within the cluster), NaN
+ * if the points span fewer than two distinct distances (or nothing has been
+ * measured).  FP64.
+ *   dmax  > 0, the largest distance fitted (min(Lx,Ly)/2 is the usual choice)
+ *   xi    dqmc_num_chains(ctx) + n_groups doubles, caller-owned: xi of every
+ *         chain in global chain order, then one per group of C(r) averaged
+ *         over the group's chains (sum of C(r) over sum of measurement counts)
+ *         -- device memory if out_on_device, else host (then synchronises).
+ * Errors: DQMC_ERR_ARG (null pointers, dmax <= 0), DQMC_ERR_CUDA. */
+int dqmc_correlation_length(dqmc_ctx* ctx, double dmax, double* xi, int out_on_device);
+
 /* Per-chain statistics since the last reset: maximum G drift seen at a
  * stabilisation point (host doubles [chain]) and accepted flips (host
  * uint64 [chain]); either pointer may be NULL. */
@@ -326,9 +347,10 @@ const char* dqmc_timing_class_name(int cls);
  * synchronisation of cudaMalloc).  It computes the stabilised equal-time
  * Green function of spin up, G = (I + B_L ... B_1)^{-1}, for ONE field
  * configuration, exactly as dqmc_set_field + dqmc_get_G would, without any
- * cudaMalloc/cudaFree: the intermediate matrices live in a fixed 4.2 MB
- * device array inside libdqmc that every GPU loading the library holds until
- * the process exits.
+ * cudaMalloc/cudaFree: the intermediate matrices live in a fixed device
+ * array inside libdqmc of 7 N_max^2 + 2 N_max + 32 doubles (N_max =
+ * DQMC_NOALLOC_MAX_N: 459,296 doubles, 3.67 MB) that every GPU loading the
+ * library holds until the process exits.
  *   params: Lx, Ly, t, U, beta, dtau and stab_interval are used (validated as
  *           for dqmc_init); n_chains, delay_k and precision are ignored.
  *           Lx*Ly must not exceed DQMC_NOALLOC_MAX_N (else DQMC_ERR_ARG).
@@ -336,10 +358,13 @@ const char* dqmc_timing_class_name(int cls);
  *   G_out:  device pointer, double [N][N] row-major (caller-owned).
  *   stream: cudaStream_t or NULL; the call synchronises it before returning.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
- * GPU (other streams, other host threads) race and must be serialised.
- * Returns DQMC_ERR_NAN if a pivot was singular or non-finite. */
+ * device, with that device current).  Every call ends by reading a status
+ * word back to the host and synchronising `stream`, so the function must
+ * never be called while `stream` is being captured into a CUDA graph.  All
+ * calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised.
+ * Returns DQMC_ERR_NAN if a pivot was singular or non-finite;
+ * dqmc_last_cuda_error names the CUDA error behind a DQMC_ERR_CUDA. */
 #define DQMC_NOALLOC_MAX_N 256
 int dqmc_green_noalloc(const dqmc_group* params, const int8_t* field, double* G_out,
                        void* stream);

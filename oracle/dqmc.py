@@ -393,7 +393,7 @@ def correlation_length(C, Lx, Ly, dmax=None):
     c = sgn * C
     pts = [(d[r], math.log(c[r])) for r in range(Lx * Ly) if 0.0 < d[r] <= dmax and c[r] > 0.0]
     n = len(pts)
-    if n < 2:
+    if len({p[0] for p in pts}) < 2:
         return float("nan")
     sd = sum(p[0] for p in pts)
     sy = sum(p[1] for p in pts)

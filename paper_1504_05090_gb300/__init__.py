@@ -145,6 +145,25 @@ class DQMC:
                    "dqmc_get_spin_correlation", lib())
         return self._split(out, lambda g: (g.n_chains, g.N))
 
+    def correlation_length(self, dmax=None, out=None):
+        """Spin correlation length of every chain and of each group's chain
+        average from the accumulated C(r) (see dqmc_correlation_length):
+        (per-chain array [chains], per-group array [groups]).  dmax defaults
+        to min(Lx, Ly) / 2 of the first group.  With `out` (a CUDA float64
+        tensor of chains + groups elements) the result stays on the device."""
+        if dmax is None:
+            dmax = 0.5 * min(self.groups[0].Lx, self.groups[0].Ly)
+        n = self.n_chains + len(self.groups)
+        if out is not None:
+            assert out.is_cuda and out.numel() == n
+            _lib.check(lib().dqmc_correlation_length(self._h, float(dmax), _ptr(out), 1),
+                       "dqmc_correlation_length", lib())
+            return out
+        host = np.empty(n)
+        _lib.check(lib().dqmc_correlation_length(self._h, float(dmax), _ptr(host), 0),
+                   "dqmc_correlation_length", lib())
+        return host[:self.n_chains], host[self.n_chains:]
+
     def reset_observables(self):
         _lib.check(lib().dqmc_reset_observables(self._h), "dqmc_reset_observables", lib())
 
@@ -348,8 +367,21 @@ class LogWeight:
     current field of every chain as a function of (t, lambda).  The forward
     value and both derivatives come from one dqmc_grad call; backward returns
     sum_c grad_out[c] * dlogW_c/dt and the same for lambda.  The inputs must
-    equal the parameters the context was built with (the field and the
-    B matrices are not re-derived from them)."""
+    equal the parameters the context was built with, t of every group and
+    lambda = arccosh(exp(dtau U / 2)) of every group (the field and the
+    B matrices are not re-derived from them); anything else raises
+    ValueError instead of returning the derivatives of another function."""
+
+    @staticmethod
+    def check_parameters(sim: DQMC, t, lam):
+        import math
+        for g in sim.groups:
+            lam_g = math.acosh(math.exp(0.5 * g.dtau * g.U))
+            if not math.isclose(float(t), g.t, rel_tol=1e-12, abs_tol=1e-300):
+                raise ValueError("LogWeight: t = %r differs from the context's t = %r" % (float(t), g.t))
+            if not math.isclose(float(lam), lam_g, rel_tol=1e-12, abs_tol=1e-300):
+                raise ValueError("LogWeight: lambda = %r differs from the context's "
+                                 "lambda = %r" % (float(lam), lam_g))
 
     @staticmethod
     def apply(sim: DQMC, t, lam):
@@ -358,6 +390,7 @@ class LogWeight:
         class _Fn(torch.autograd.Function):
             @staticmethod
             def forward(ctx, t_, lam_):
+                LogWeight.check_parameters(sim, t_.item(), lam_.item())
                 dev = torch.device("cuda")
                 dt = torch.empty(sim.n_chains, dtype=torch.float64, device=dev)
                 dl = torch.empty_like(dt)

@@ -55,6 +55,8 @@ SIGNATURES = {
     "dqmc_reset_observables": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_spin_correlation_size": (ctypes.c_int64, [ctypes.c_void_p]),
     "dqmc_get_spin_correlation": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "dqmc_correlation_length": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p,
+                                               ctypes.c_int]),
     "dqmc_get_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "dqmc_reset_stats": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_num_chains": (ctypes.c_int, [ctypes.c_void_p]),

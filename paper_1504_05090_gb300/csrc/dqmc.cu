@@ -112,6 +112,14 @@ struct Group {
   long long sstride() const { return static_cast<long long>(nc + 1) * N * N; }
 };
 
+thread_local cudaError_t g_last_cuda = cudaSuccess;  // last failing CUDA call (this thread)
+thread_local int g_last_line = 0;
+
+void record_cuda_error(cudaError_t e, int line) {
+  g_last_cuda = e;
+  g_last_line = line;
+}
+
 }  // namespace dqmc
 
 using namespace dqmc;
@@ -160,8 +168,6 @@ namespace {
 constexpr int kOzakiMinN = 64;  // smaller matrices stay on the FP64 pipe
 constexpr double kTuneMargin = 0.05;  // probe drift must stay below 5% of the target
 
-thread_local cudaError_t g_last_cuda = cudaSuccess;  // last failing CUDA call (this thread)
-thread_local int g_last_line = 0;
 
 #define DQ_CK(call)                                 \
   do {                                              \
@@ -1089,8 +1095,17 @@ int dqmc_measure_Gtau_origins(dqmc_ctx* ctx, int n_origins, double* out, int out
       return DQMC_OK;
     };
     rc = run();
-    if (rc != DQMC_OK)  // best effort: give the chains their own field back
-      cudaMemcpy(g.field, saved, nf, cudaMemcpyDeviceToDevice);
+    if (rc != DQMC_OK) {
+      // Best effort: give the chains their own field back, ordered after any
+      // rotation still queued on the group's stream, and rebuild the stacks
+      // and G from it.  If this fails too, the context needs
+      // dqmc_recompute_G (or dqmc_set_field) before further sweeps.
+      cudaStreamSynchronize(g.st);
+      cudaGetLastError();
+      if (cudaMemcpyAsync(g.field, saved, nf, cudaMemcpyDeviceToDevice, g.st) == cudaSuccess &&
+          rebuild(ctx, g) == DQMC_OK && load_working(ctx, g) == DQMC_OK)
+        cudaStreamSynchronize(g.st);
+    }
     cudaFree(saved);
     if (!out_on_device) cudaFree(acc);
     if (rc != DQMC_OK) return rc;
@@ -1248,6 +1263,25 @@ int dqmc_get_spin_correlation(const dqmc_ctx* ctx, double* out) {
     off += n;
   }
   DQ_CK(cudaStreamSynchronize(ctx->st));
+  return DQMC_OK;
+}
+
+int dqmc_correlation_length(dqmc_ctx* ctx, double dmax, double* xi, int out_on_device) {
+  if (!ctx || !xi || !(dmax > 0.0)) return DQMC_ERR_ARG;
+  const int ng = static_cast<int>(ctx->g.size());
+  // per group: C + 1 results (chains, then the chain average), staged in the
+  // group's G(tau) buffer and copied to the caller's layout
+  size_t chain_off = 0;
+  for (int gi = 0; gi < ng; ++gi) {
+    Group& g = ctx->g[gi];
+    DQ_LAUNCH_C(ctx, kTMisc, launch_corr_length(g.spin, g.obs, g.C, g.p.Lx, g.p.Ly, dmax, g.gout,
+                                                  ctx->st));
+    const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    DQ_CK(cudaMemcpyAsync(xi + chain_off, g.gout, g.C * sizeof(double), kind, ctx->st));
+    DQ_CK(cudaMemcpyAsync(xi + ctx->total + gi, g.gout + g.C, sizeof(double), kind, ctx->st));
+    chain_off += g.C;
+  }
+  if (!out_on_device) DQ_CK(cudaStreamSynchronize(ctx->st));
   return DQMC_OK;
 }
 

@@ -556,12 +556,16 @@ cudaError_t launch_gj_cluster(double* A, long long sA, double* Ainv, long long s
   // matrix over 4 CTAs, two of which fit on an SM (512 threads x 64
   // registers), so that twice as many warps hide the step latency; large
   // batches keep 2 CTAs per matrix.
-  static int nsm = 0;
+  // SM count of the current device, cached per device (a process may drive
+  // several GPUs)
+  constexpr int kMaxDev = 64;
+  static int nsm_of[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cudaErrorInvalidDevice;
+  int nsm = (dev >= 0 && dev < kMaxDev) ? nsm_of[dev] : 0;
   if (nsm == 0) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-      nsm = 1;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 1;
+    if (dev >= 0 && dev < kMaxDev) nsm_of[dev] = nsm;
   }
   if (pair) {  // float-pair elimination: A becomes an array of pairs in place
     const long long count = static_cast<long long>(batch - 1) * sA + static_cast<long long>(n) * n;

@@ -12,6 +12,8 @@
 // G_dn = I - P G_up^T P (P = diag((-1)^{x+y})), so G_dn,ii = 1 - G_up,ii.
 #include <cooperative_groups.h>
 
+#include <math_constants.h>
+
 #include <type_traits>
 
 #include "common.cuh"
@@ -685,6 +687,85 @@ __global__ void __launch_bounds__(256) k_observables(const double* G64, int Lx, 
 }
 
 // ---------------------------------------------------------------------------
+// Correlation length of Sec. 4 (Fig. 5): least-squares line through
+// (|r|, ln c(r)), c(r) = (-1)^(dx+dy) C(r) the staggered correlation,
+// |r| = sqrt(min(dx, Lx-dx)^2 + min(dy, Ly-dy)^2), over 0 < |r| <= dmax and
+// c(r) > 0; xi = -1/slope (+inf for a slope >= 0, nan below two distinct
+// distances).  C(r) = spin[c][r] / obs[c][3] for block c < C; block C takes
+// the chain average sum_c spin[c][r] / sum_c obs[c][3].  One thread per r.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_corr_length(const double* spin, const double* obs, int C,
+                                                    int Lx, int Ly, double dmax, double* out) {
+  const int b = blockIdx.x, N = Lx * Ly;
+  __shared__ double cnt_sh;
+  if (threadIdx.x == 0) {
+    double cnt = 0.0;
+    if (b < C) {
+      cnt = obs[static_cast<size_t>(b) * 4 + 3];
+    } else {
+      for (int c = 0; c < C; ++c) cnt += obs[static_cast<size_t>(c) * 4 + 3];
+    }
+    cnt_sh = cnt;
+  }
+  __syncthreads();
+  double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // n, S_d, S_y, S_dd, S_dy
+  double dmin = CUDART_INF, dmaxp = -1.0;     // smallest / largest distance used
+  for (int r = threadIdx.x; r < N; r += blockDim.x) {
+    double v = 0.0;
+    if (b < C) {
+      v = spin[static_cast<size_t>(b) * N + r];
+    } else {
+      for (int c = 0; c < C; ++c) v += spin[static_cast<size_t>(c) * N + r];
+    }
+    const int dx = r % Lx, dy = r / Lx;
+    const double cr = (((dx + dy) & 1) ? -v : v) / cnt_sh;
+    const int ax = min(dx, Lx - dx), ay = min(dy, Ly - dy);
+    const double d = sqrt(static_cast<double>(ax * ax + ay * ay));
+    if (d > 0.0 && d <= dmax && cr > 0.0) {
+      const double y = log(cr);
+      s[0] += 1.0;
+      s[1] += d;
+      s[2] += y;
+      s[3] += d * d;
+      s[4] += d * y;
+      dmin = fmin(dmin, d);
+      dmaxp = fmax(dmaxp, d);
+    }
+  }
+  __shared__ double red[8][7];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) s[q] += __shfl_xor_sync(0xFFFFFFFFu, s[q], o);
+    dmin = fmin(dmin, __shfl_xor_sync(0xFFFFFFFFu, dmin, o));
+    dmaxp = fmax(dmaxp, __shfl_xor_sync(0xFFFFFFFFu, dmaxp, o));
+  }
+  if (lane == 0) {
+    for (int q = 0; q < 5; ++q) red[w][q] = s[q];
+    red[w][5] = dmin;
+    red[w][6] = dmaxp;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double lo = CUDART_INF, hi = -1.0;
+    for (int q = 0; q < nw; ++q) {
+      for (int k = 0; k < 5; ++k) t[k] += red[q][k];
+      lo = fmin(lo, red[q][5]);
+      hi = fmax(hi, red[q][6]);
+    }
+    double xi = CUDART_NAN;
+    const double den = t[0] * t[3] - t[1] * t[1];
+    if (t[0] >= 2.0 && hi > lo && den > 0.0) {
+      const double slope = (t[0] * t[4] - t[1] * t[2]) / den;
+      xi = (slope < 0.0) ? -1.0 / slope : CUDART_INF;
+    }
+    out[b] = xi;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host launch wrappers.
 // ---------------------------------------------------------------------------
 cudaError_t launch_init_field(int8_t* field, int C, int L, int N, int chain0, uint64_t seed,
@@ -767,6 +848,12 @@ cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* d
 cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
                                double* spin, cudaStream_t st) {
   k_observables<<<C, 256, 0, st>>>(G64, Lx, Ly, t, obs, spin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_corr_length(const double* spin, const double* obs, int C, int Lx, int Ly,
+                               double dmax, double* out, cudaStream_t st) {
+  k_corr_length<<<C + 1, 256, 0, st>>>(spin, obs, C, Lx, Ly, dmax, out);
   return cudaGetLastError();
 }
 

@@ -70,6 +70,10 @@ struct GemmArgs {
   double alpha, beta;
 };
 
+// Remember the CUDA error (and library source line) that makes a C-ABI call
+// on this host thread return DQMC_ERR_CUDA, for dqmc_last_cuda_error.
+void record_cuda_error(cudaError_t e, int line);
+
 cudaError_t launch_init_field(int8_t* field, int C, int L, int N, int chain0, uint64_t seed,
                               cudaStream_t st);
 template <typename T>
@@ -85,6 +89,11 @@ cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* d
                                cudaStream_t st);
 cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
                                double* spin, cudaStream_t st);
+
+// Correlation length of every chain (out[0..C-1]) and of the chain average
+// (out[C]) from the accumulated spin correlation [C][N] and observables [C][4].
+cudaError_t launch_corr_length(const double* spin, const double* obs, int C, int Lx, int Ly,
+                               double dmax, double* out, cudaStream_t st);
 
 cudaError_t launch_gemm(const GemmArgs& a, int batch, cudaStream_t st);
 // The same product on the tcgen05 tensor cores with FP64-level accuracy

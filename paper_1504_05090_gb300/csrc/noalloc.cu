@@ -10,7 +10,8 @@
 // for G; the intermediate matrices live in the fixed array below.
 //
 // The scratch array is a file-scope __device__ array: every GPU that loads
-// libdqmc holds it (4.2 MB) until the process exits.  In host code its name
+// libdqmc holds it (kScratchDoubles = 459,296 doubles, 3.67 MB) until the
+// process exits.  In host code its name
 // is only a host-side stand-in, so its device address is looked up with
 // cudaGetSymbolAddress once per device (with that device current) and passed
 // to the kernels.  All calls share the one array, which keeps the contents
@@ -32,6 +33,8 @@ constexpr int kNoAllocMaxN = DQMC_NOALLOC_MAX_N;
 constexpr size_t kNN = static_cast<size_t>(kNoAllocMaxN) * kNoAllocMaxN;
 // Layout: U0, U1, T0, T1, X, Rtil, Mid (7 N x N), D0, D1 (2 N), status word.
 constexpr size_t kScratchDoubles = 7 * kNN + 2 * kNoAllocMaxN + 32;
+static_assert(DQMC_MAX_SIDE * DQMC_MAX_SIDE <= DQMC_NOALLOC_MAX_N,
+              "every cluster that dqmc_init accepts fits the scratch array");
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
@@ -42,12 +45,18 @@ std::mutex g_scratch_mu;
 // Device address of the scratch array on the current device (looked up once).
 int scratch_address(double** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DQMC_ERR_CUDA;
+  const cudaError_t eg = cudaGetDevice(&dev);
+  if (eg != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    record_cuda_error(eg != cudaSuccess ? eg : cudaErrorInvalidDevice, __LINE__);
+    return DQMC_ERR_CUDA;
+  }
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
       cudaGetLastError();
+      record_cuda_error(e != cudaSuccess ? e : cudaErrorInvalidSymbol, __LINE__);
       return DQMC_ERR_CUDA;
     }
     g_scratch_ptr[dev] = static_cast<double*>(p);
@@ -116,9 +125,13 @@ extern "C" int dqmc_green_noalloc(const dqmc_group* p, const int8_t* field, doub
   double* D[2] = {s + 7 * nn, s + 7 * nn + N};
   int* status = reinterpret_cast<int*>(s + 7 * nn + 2 * N);
 
-#define NA_CK(call)                                  \
-  do {                                               \
-    if ((call) != cudaSuccess) return DQMC_ERR_CUDA; \
+#define NA_CK(call)                   \
+  do {                                \
+    const cudaError_t e_ = (call);    \
+    if (e_ != cudaSuccess) {          \
+      record_cuda_error(e_, __LINE__); \
+      return DQMC_ERR_CUDA;           \
+    }                                 \
   } while (0)
   NA_CK(cudaMemsetAsync(status, 0, sizeof(int), st));
 

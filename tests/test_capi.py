@@ -161,3 +161,33 @@ def test_every_timed_kernel_class_has_a_roofline_formula(libpath):
                 assert bound is None
             else:
                 assert bound in ("alu", "alu64", "alu32x2", "tensor") and work > 0, (name, prec)
+
+
+def test_correlation_length_argument_checks_without_gpu(libpath):
+    import numpy as np
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    buf = np.zeros(4)
+    assert lib.dqmc_correlation_length(None, 4.0, buf.ctypes.data_as(ctypes.c_void_p), 0) == -1
+
+
+def test_logweight_rejects_parameters_other_than_the_contexts():
+    """LogWeight differentiates log W of the context's own B matrices; a t or
+    lambda that differs from the context's must raise, not return the
+    derivatives of another function (host logic, no GPU)."""
+    import math
+    import paper_1504_05090_gb300 as pkg
+
+    class FakeSim:
+        groups = [pkg.Group(Lx=4, Ly=4, t=0.25, U=2.0, dtau=0.125),
+                  pkg.Group(Lx=8, Ly=8, t=0.25, U=2.0, dtau=0.125)]
+
+    lam = math.acosh(math.exp(0.5 * 0.125 * 2.0))
+    pkg.LogWeight.check_parameters(FakeSim, 0.25, lam)
+    with pytest.raises(ValueError):
+        pkg.LogWeight.check_parameters(FakeSim, 0.26, lam)
+    with pytest.raises(ValueError):
+        pkg.LogWeight.check_parameters(FakeSim, 0.25, lam * (1 + 1e-9))
+    FakeSim.groups.append(pkg.Group(Lx=4, Ly=4, t=0.25, U=3.0, dtau=0.125))
+    with pytest.raises(ValueError):  # groups with different lambda: no single (t, lambda)
+        pkg.LogWeight.check_parameters(FakeSim, 0.25, lam)

@@ -330,6 +330,83 @@ def test_autograd_function_backward():
         assert lam.grad.item() == pytest.approx(float(np.sum(dl * [1, 2, 3])), rel=1e-12)
 
 
+def test_autograd_function_rejects_other_parameters():
+    import torch
+    import paper_1504_05090_gb300 as pkg
+    g = _grp(4, 4, C=2)
+    with _sim([g], seed=4) as sim:
+        lam = torch.tensor(o.hs_lambda(2.0, 0.125), dtype=torch.float64, requires_grad=True)
+        with pytest.raises(ValueError):
+            pkg.LogWeight.apply(sim, torch.tensor(0.3, dtype=torch.float64, requires_grad=True), lam)
+
+
+def test_gradient_expectations_give_double_occupancy_and_kinetic_energy():
+    """The gradient workload (8x8, U = 2, beta = 10, dtau = 0.125, L = 80, 512
+    FP64 chains): the field averages of the two derivatives of log W give
+    the directly measured equal-time observables, within 3 sigma over the
+    chains (independent samples):
+      d    = 1/2 - coth(lambda) <dlogW/dlambda> / (2 N L)   (from d ln Z/dU),
+      ekin = -t <dlogW/dt> / (beta N)                        (Hellmann-Feynman),
+    against <n_up n_dn> and the kinetic energy per site accumulated at the
+    stabilisation points of the same sweeps."""
+    import math
+    g = _grp(8, 8, U=2.0, beta=10.0, dtau=0.125, ns=10, k=16, C=512)
+    N, L = g.N, g.L
+    lam = o.hs_lambda(g.U, g.dtau)
+    with _sim([g], seed=17) as sim:
+        sim.sweep(30, measure=False)
+        sim.reset_observables()
+        n_meas = 20
+        dt_sum = np.zeros(g.n_chains)
+        dl_sum = np.zeros(g.n_chains)
+        for _ in range(n_meas):
+            sim.sweep(1, measure=True)
+            dt, dl, _ = sim.grad()
+            dt_sum += dt
+            dl_sum += dl
+        obs = sim.observables()
+    d_meas = obs[:, 1] / obs[:, 3]
+    e_meas = obs[:, 2] / obs[:, 3]
+    d_grad = 0.5 - (dl_sum / n_meas) / math.tanh(lam) / (2 * N * L)
+    e_grad = -g.t * (dt_sum / n_meas) / (g.beta * N)
+    for est, ref in ((d_grad, d_meas), (e_grad, e_meas)):
+        diff = est - ref
+        sigma = np.std(diff, ddof=1) / math.sqrt(len(diff))
+        assert abs(np.mean(diff)) < 3 * sigma, (np.mean(diff), sigma)
+        assert abs(np.mean(diff)) < 1e-2 * abs(np.mean(ref))
+
+
+# -- correlation length of Sec. 4 (Fig. 5) ------------------------------------
+def test_correlation_length_matches_oracle():
+    """xi of every chain and of each group's chain average from the
+    accumulated C(r), against the oracle's fit of the same C(r) (1e-12);
+    before any measurement every xi is NaN; device output equals host."""
+    import torch
+    groups = [_grp(8, 8, U=2.0, beta=4.0, dtau=0.125, ns=8, k=16, C=4),
+              _grp(6, 4, U=3.0, beta=2.0, dtau=0.1, ns=5, k=8, C=3, prec="df32")]
+    dmax = 3.0
+    with _sim(groups, seed=41) as sim:
+        xc, xg = sim.correlation_length(dmax)
+        assert np.all(np.isnan(xc)) and np.all(np.isnan(xg))
+        sim.sweep(4, measure=True)
+        xc, xg = sim.correlation_length(dmax)
+        spin, obs = sim.spin_correlation(), sim.observables()
+        chain = 0
+        for gi, g in enumerate(groups):
+            c0 = chain
+            for c in range(g.n_chains):
+                ref = o.correlation_length(spin[gi][c] / obs[chain, 3], g.Lx, g.Ly, dmax)
+                assert xc[chain] == pytest.approx(ref, rel=1e-12, nan_ok=True), (gi, c)
+                chain += 1
+            avg = spin[gi].sum(axis=0) / obs[c0:chain, 3].sum()
+            ref = o.correlation_length(avg, g.Lx, g.Ly, dmax)
+            assert xg[gi] == pytest.approx(ref, rel=1e-12, nan_ok=True), gi
+        assert np.isfinite(xg).all()
+        dev = torch.empty(sim.n_chains + len(groups), dtype=torch.float64, device="cuda")
+        sim.correlation_length(dmax, out=dev)
+        np.testing.assert_array_equal(dev.cpu().numpy(), np.concatenate([xc, xg]))
+
+
 # -- df32 working precision (float pairs): FP64-class decisions ---------------
 @pytest.mark.parametrize("Lx,Ly,beta,dtau,ns,k", [(4, 4, 2.0, 0.125, 4, 4), (6, 6, 2.0, 0.1, 6, 8),
                                                   (8, 8, 1.0, 0.125, 3, 16)])
@@ -427,32 +504,64 @@ def test_fp32_path_replay_and_drift():
 
 
 # -- full-size sample: 16x16, L = 160, 64 chains (the benchmarked launch) -----
+@pytest.fixture(scope="module")
+def full_size_oracle():
+    """Oracle results for chains 0 and 63 of the benchmarked workload, computed
+    in two spawned processes (a process forked after CUDA initialisation
+    would hang)."""
+    import multiprocessing as mp
+
+    from tests import oracle_jobs
+    with mp.get_context("spawn").Pool(2) as pool:
+        res = pool.map(oracle_jobs.full_size_chain, [0, 63])
+    return dict(zip((0, 63), res))
+
+
 @pytest.mark.slow
-def test_full_size_16x16_sampled_chains():
-    g = _grp(16, 16, U=2.0, beta=20.0, dtau=0.125, ns=10, k=32, C=64)
-    p = _params(g)
-    with _sim([g], seed=0) as sim:
+@pytest.mark.parametrize("prec,gtau_tol", [("fp64", 1e-10), ("df32", 1e-9)])
+def test_full_size_16x16_sampled_chains(prec, gtau_tol, full_size_oracle):
+    """The benchmarked launch itself -- 16x16, L = 160, 64 chains, k = 32,
+    n_s = 10, the default Metropolis split (2 CTAs x 512 threads per chain in
+    float pairs) -- element by element against the oracle on chains 0 and 63
+    for one full sweep: initial fields and G(0), the field after the sweep
+    and the accepted count (exact), G of both spins (1e-10 relative), the
+    observables and C(r) (1e-9) and G_k(tau) of the new field (FP64 groups
+    1e-10, float-pair propagation 1e-9 of the maximum)."""
+    from tests import oracle_jobs
+    f = oracle_jobs.FULL
+    g = _grp(f["Lx"], f["Ly"], U=f["U"], beta=f["beta"], dtau=f["dtau"], ns=f["n_s"], k=32, C=64,
+             prec=prec)
+    with _sim([g], seed=f["seed"]) as sim:
         f0 = sim.field()[0]
-        for c in (0, 63):
-            assert np.array_equal(f0[c], o.initial_field(0, c, g.N, g.L))
-        ch0 = o.Chain(p, seed=0, chain=0)
-        assert _rel(sim.G(0, 0), ch0.green(0, 1)) < GTOL
+        for c, ref in full_size_oracle.items():
+            assert np.array_equal(f0[c], ref["field0"]), c
+            assert _rel(sim.G(c, 0), ref["G0_up"]) < GTOL, c
         sim.sweep(1)
-        out = ch0.sweep()
-        assert np.array_equal(sim.field()[0][0], ch0.field)
-        assert _rel(sim.G(0, 0), out["G_up"]) < GTOL
+        fields = sim.field()[0]
         drift, acc = sim.stats()
-        assert acc[0] == out["accepted"]
+        obs = sim.observables()
+        spin = sim.spin_correlation()[0]
+        for c, ref in full_size_oracle.items():
+            assert np.array_equal(fields[c], ref["field"]), c
+            assert acc[c] == ref["accepted"], c
+            assert _rel(sim.G(c, 0), ref["G_up"]) < GTOL, c
+            assert _rel(sim.G(c, 1), ref["G_dn"]) < GTOL, c
+            assert obs[c, 3] == ref["n_meas"]
+            np.testing.assert_allclose(obs[c, :3], ref["obs"], rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(spin[c], ref["spin"], rtol=1e-9, atol=1e-12)
         assert np.all(drift < 1e-8)
-        # spin correlation: chain 0 element by element against the oracle; every
-        # chain through properties that hold at any size
-        spin, obs = sim.spin_correlation()[0], sim.observables()
-        np.testing.assert_allclose(spin[0], np.sum(out["spin"], axis=0), rtol=1e-9, atol=1e-12)
+        gt = sim.gtau()[0]
+        for c, ref in full_size_oracle.items():
+            np.testing.assert_allclose(gt[c], ref["gtau"], rtol=0,
+                                       atol=gtau_tol * np.max(np.abs(ref["gtau"])))
+        # every chain through properties that hold at any size
         # C(r) = C(-r): S^z_i S^z_{i+r} summed over i is symmetric in r
         minus = [((-dx) % 16) + 16 * ((-dy) % 16) for dy in range(16) for dx in range(16)]
         np.testing.assert_allclose(spin[:, minus], spin, rtol=1e-12, atol=1e-14)
         # C(0) = <(S^z)^2> = (n - 2 docc) / 4 per site, from the separate observables
         np.testing.assert_allclose(spin[:, 0], (obs[:, 0] - 2.0 * obs[:, 1]) / 4.0, rtol=1e-12)
+        # G_k(0) + G_k(beta) = 1 for every chain and momentum (G(L,0) = I - G(0))
+        np.testing.assert_allclose(gt[:, 0, :] + gt[:, -1, :], 1.0, rtol=0, atol=1e-9)
 
 
 def test_chain_offset_makes_results_independent_of_the_split():

@@ -51,7 +51,10 @@ def test_green_noalloc_matches_regular_path_twice(Lx, Ly, U, beta, dtau, ns):
         assert _rel(G_dev.cpu().numpy(), refs[c]) < GTOL
 
 
-def test_green_noalloc_rejects_oversize():
+def test_green_noalloc_rejects_sizes_beyond_the_side_limit():
+    """Lx = 18 exceeds DQMC_MAX_SIDE and is rejected with DQMC_ERR_ARG.  (The
+    separate N <= DQMC_NOALLOC_MAX_N check cannot be reached through a valid
+    side length: a static_assert keeps DQMC_MAX_SIDE^2 within it.)"""
     import torch
 
     import paper_1504_05090_gb300 as pkg
