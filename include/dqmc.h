@@ -135,6 +135,38 @@ int dqmc_sweep(dqmc_ctx* ctx, int n_sweeps, int measure);
 int dqmc_autotune(const dqmc_group* groups, int n_groups, double drift_target, uint64_t seed,
                   void* stream, dqmc_group* out);
 
+/* Tile shapes of one group's kernels (implementation choices only: results
+ * are bit-identical for every allowed value).
+ *   kron_nv     vectors per CTA of the FP64 Kronecker products with
+ *               exp(-+dtau K) = E_y (x) E_x of Eq. (2) (UDV stack, G(tau)
+ *               propagation of FP64 groups, gradient): 1, 2, 4, 8 or 16
+ *               (<= N); 0 = built-in (4)
+ *   wrap_nv     vectors per CTA of the slice wrap B_l G B_l^{-1} in the
+ *               working precision (float-pair groups propagate G(tau) with
+ *               twice as many): same values; 0 = built-in
+ *   metro_ctas  CTAs per chain of the Metropolis pass, one thread-block
+ *               cluster (as dqmc_set_metropolis_split, for this group): 1, 2
+ *               or 4 (4 * metro_ctas <= N); 0 = the context's setting */
+typedef struct {
+    int32_t kron_nv, wrap_nv, metro_ctas;
+} dqmc_tiles;
+
+/* Set the tile shapes of group `group` (creation order).  Drops captured
+ * sweep graphs if anything changes.  Errors: DQMC_ERR_ARG. */
+int dqmc_set_tiles(dqmc_ctx* ctx, int group, const dqmc_tiles* tiles);
+
+/* The tile shapes in effect for group `group` (built-in choices resolved). */
+int dqmc_get_tiles(const dqmc_ctx* ctx, int group, dqmc_tiles* out);
+
+/* Tile autotuner: for each group (alone, with its full chain count) time one
+ * sweep per candidate (kron_nv, wrap_nv, metro_ctas) in {(2,2,1), (4,4,2),
+ * (8,8,4)} with the per-kernel-class timing, and take for each parameter the
+ * candidate whose kernel class (stack_kron, wrap, metropolis) was fastest.
+ * out: host array [n_groups].  Creates and destroys its own contexts on
+ * `stream` (seed as dqmc_init).  Errors: as dqmc_init. */
+int dqmc_autotune_tiles(const dqmc_group* groups, int n_groups, uint64_t seed, void* stream,
+                        dqmc_tiles* out);
+
 /* Sweeps are replayed as one CUDA graph per measure flag (captured at the
  * first dqmc_sweep: one branch per group, the groups run concurrently); with
  * on = 0, or while timing is enabled, kernels are launched one by one on the
@@ -318,6 +350,22 @@ int64_t dqmc_launch_count(const dqmc_ctx* ctx);
 #define DQMC_GEMM_TENSOR 0
 #define DQMC_GEMM_FP64 1
 int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode);
+
+/* QR factorisation of the UDV stack steps (Sec. 2, the stabilisation of
+ * Eq. (3)):
+ *   DQMC_QR_BLOCKED (default): the columns of each step's product are sorted
+ *     by decreasing norm once (pre-pivoting), then factorised without further
+ *     pivoting by blocked Householder QR: FP64 panels of 32 columns, the
+ *     trailing updates and the accumulation of Q on the tensor-core FP64
+ *     products.  Used where those products are (DQMC_GEMM_TENSOR, N >= 64).
+ *   DQMC_QR_PIVOTED: Householder QR with column pivoting on the FP64 pipe
+ *     (always used for N < 64 and in DQMC_GEMM_FP64 mode).
+ * Both give X = U D T with |diag| T = 1; G agrees between them to the
+ * conditioning of the problem.  Drops captured sweep graphs.  Errors:
+ * DQMC_ERR_ARG. */
+#define DQMC_QR_BLOCKED 0
+#define DQMC_QR_PIVOTED 1
+int dqmc_set_qr_mode(dqmc_ctx* ctx, int mode);
 
 /* CTAs per chain in the Metropolis pass (the site loop of Sec. 2 with the
  * delayed updates of G, Eq. (3)): 1, 2 or 4 CTAs of one thread-block cluster

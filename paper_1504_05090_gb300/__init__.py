@@ -14,7 +14,7 @@ import numpy as np
 
 from . import _lib
 
-__all__ = ["Group", "DQMC", "LogWeight", "DqmcError", "n_slices", "autotune"]
+__all__ = ["Group", "DQMC", "LogWeight", "DqmcError", "n_slices", "autotune", "autotune_tiles"]
 
 DqmcError = _lib.DqmcError
 _LIB = None
@@ -188,10 +188,29 @@ class DQMC:
         code = {"tensor": _lib.DQMC_GEMM_TENSOR, "fp64": _lib.DQMC_GEMM_FP64}[mode]
         _lib.check(lib().dqmc_set_gemm_mode(self._h, code), "dqmc_set_gemm_mode", lib())
 
+    def set_qr_mode(self, mode):
+        """'blocked' (default: pre-pivoted blocked Householder QR on the tensor
+        cores) or 'pivoted' (column-pivoted QR on the FP64 pipe)."""
+        code = {"blocked": _lib.DQMC_QR_BLOCKED, "pivoted": _lib.DQMC_QR_PIVOTED}[mode]
+        _lib.check(lib().dqmc_set_qr_mode(self._h, code), "dqmc_set_qr_mode", lib())
+
     def set_metropolis_split(self, ctas_per_chain=0):
         """CTAs per chain in the Metropolis pass: 1, 2, 4, or 0 for automatic."""
         _lib.check(lib().dqmc_set_metropolis_split(self._h, int(ctas_per_chain)),
                    "dqmc_set_metropolis_split", lib())
+
+    def set_tiles(self, group, kron_nv=0, wrap_nv=0, metro_ctas=0):
+        """Tile shapes of one group's kernels (see dqmc_set_tiles); 0 = built-in."""
+        t = _lib.DqmcTiles(int(kron_nv), int(wrap_nv), int(metro_ctas))
+        _lib.check(lib().dqmc_set_tiles(self._h, int(group), ctypes.byref(t)), "dqmc_set_tiles",
+                   lib())
+
+    def tiles(self, group):
+        """Tile shapes in effect for one group: dict(kron_nv, wrap_nv, metro_ctas)."""
+        t = _lib.DqmcTiles()
+        _lib.check(lib().dqmc_get_tiles(self._h, int(group), ctypes.byref(t)), "dqmc_get_tiles",
+                   lib())
+        return dict(kron_nv=t.kron_nv, wrap_nv=t.wrap_nv, metro_ctas=t.metro_ctas)
 
     def timing(self, on=True):
         """Enable/disable per-launch CUDA-event timing by kernel class."""
@@ -283,6 +302,19 @@ def autotune(groups, drift_target=1e-6, seed=0):
                          n_chains=g.n_chains, stab_interval=int(o.stab_interval),
                          delay_k=int(o.delay_k), precision=g.precision))
     return res
+
+
+def autotune_tiles(groups, seed=0):
+    """Tile shapes chosen by the library's tile autotuner for each group
+    (see dqmc_autotune_tiles): a list of dict(kron_nv, wrap_nv, metro_ctas)."""
+    import torch
+    groups = list(groups)
+    arr = (_lib.DqmcGroup * len(groups))(*[g._c() for g in groups])
+    out = (_lib.DqmcTiles * len(groups))()
+    st = torch.cuda.current_stream().cuda_stream
+    _lib.check(lib().dqmc_autotune_tiles(arr, len(groups), int(seed), ctypes.c_void_p(st), out),
+               "dqmc_autotune_tiles", lib())
+    return [dict(kron_nv=o.kron_nv, wrap_nv=o.wrap_nv, metro_ctas=o.metro_ctas) for o in out]
 
 
 def trotter_extrapolate(dtaus, gks, beta, M):

@@ -17,6 +17,8 @@ DQMC_FP32 = 1
 DQMC_DF32 = 2
 DQMC_GEMM_TENSOR = 0
 DQMC_GEMM_FP64 = 1
+DQMC_QR_BLOCKED = 0
+DQMC_QR_PIVOTED = 1
 MAX_SIDE = 16
 MAX_DELAY = 32
 
@@ -31,6 +33,11 @@ class DqmcGroup(ctypes.Structure):
                 ("beta", ctypes.c_double), ("dtau", ctypes.c_double),
                 ("n_chains", ctypes.c_int32), ("stab_interval", ctypes.c_int32),
                 ("delay_k", ctypes.c_int32), ("precision", ctypes.c_int32)]
+
+
+class DqmcTiles(ctypes.Structure):
+    _fields_ = [("kron_nv", ctypes.c_int32), ("wrap_nv", ctypes.c_int32),
+                ("metro_ctas", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes); this list is also the export check of the tests.
@@ -62,10 +69,15 @@ SIGNATURES = {
     "dqmc_num_chains": (ctypes.c_int, [ctypes.c_void_p]),
     "dqmc_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "dqmc_set_gemm_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "dqmc_set_qr_mode": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_set_metropolis_split": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_use_graphs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_autotune": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_int, ctypes.c_double,
                                      ctypes.c_uint64, ctypes.c_void_p, ctypes.POINTER(DqmcGroup)]),
+    "dqmc_set_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(DqmcTiles)]),
+    "dqmc_get_tiles": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(DqmcTiles)]),
+    "dqmc_autotune_tiles": (ctypes.c_int, [ctypes.POINTER(DqmcGroup), ctypes.c_int, ctypes.c_uint64,
+                                           ctypes.c_void_p, ctypes.POINTER(DqmcTiles)]),
     "dqmc_timing_enable": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "dqmc_timing_read": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                         ctypes.c_int]),

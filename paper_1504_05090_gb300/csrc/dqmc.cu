@@ -103,6 +103,9 @@ struct Group {
   double* qrs = nullptr;   // [C][2N] column norms of the QR
   void* oz = nullptr;      // digit slices of the tensor-core FP64 GEMM
   int oz_batch = 0;
+  QrbWork qrb{};           // blocked-QR workspace (tensor-core path)
+  // tile shapes (dqmc_set_tiles; 0 = the built-in choice)
+  int tile_kron = 0, tile_wrap = 0, tile_metro = 0;
   cudaStream_t st = nullptr;   // stream this group's work is enqueued on
   cudaStream_t cap = nullptr;  // the group's own stream (graph capture branches)
   cudaEvent_t join = nullptr;
@@ -137,6 +140,7 @@ struct dqmc_ctx {
   std::vector<Group> g;
   cudaStream_t st = nullptr;
   int gemm_mode = DQMC_GEMM_TENSOR;
+  int qr_mode = DQMC_QR_BLOCKED;
   // CUDA graph of one sweep of all groups (index: measure flag), captured on
   // cap_main with one forked branch per group, replayed on st.
   bool use_graph = true;
@@ -281,6 +285,7 @@ KronArgs kron_base(const Group& g, int kind, int nv) {
 }
 
 int kron_nv(const Group& g, bool fp64) {
+  if (g.tile_kron > 0) return std::min(g.tile_kron, g.N);
   // Vectors per CTA of the FP64 Kronecker transforms (stack products, G(tau)
   // of FP64 groups, gradient): small tiles, so that several CTAs share an SM
   // and their independent FMA chains keep the FP64 pipe busy (measured on the
@@ -298,6 +303,7 @@ int kron_nv(const Group& g, bool fp64) {
 // (4 vectors, about 17 KB of shared memory at N = 256).
 template <typename T>
 int wrap_nv(const Group& g) {
+  if (g.tile_wrap > 0) return std::min(g.tile_wrap, g.N);
   if (sizeof(T) == 8 && !std::is_same<T, df32>::value) return kron_nv(g, true);
   return std::min(4, g.N);
 }
@@ -312,9 +318,28 @@ GemmArgs gemm0(int n) {
 // FP64 products: on the tensor cores (digit-sliced, FP64-level accuracy) for
 // N >= kOzakiMinN unless the context asks for the FP64 pipe.
 cudaError_t gemm(dqmc_ctx* ctx, Group& g, const GemmArgs& m, int batch) {
-  if (ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz)
+  if (ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz) {
+    // the split kernel (plus the balance pass) besides the MMA kernel, per chunk
+    const int chunks = (batch + g.oz_batch - 1) / g.oz_batch;
+    ctx->launches += static_cast<long long>(chunks) * (m.balance ? 3 : 2) - 1;
     return launch_gemm_ozaki(m, batch, g.oz, g.oz_batch, ctx->d_status, g.st);
+  }
   return launch_gemm(m, batch, g.st);
+}
+
+// QR of the stack step X = B..B (U D) (rows of g.X = columns of X) into the
+// stack entry (Q^T at Qt, D at Dv) and g.Rtil: the blocked, pre-pivoted QR
+// with tensor-core updates where the tensor-core products are in use, the
+// column-pivoted cluster QR on the FP64 pipe otherwise.
+cudaError_t stack_qr(dqmc_ctx* ctx, Group& g, double* Qt, double* Dv) {
+  const long long sD = static_cast<long long>(g.nc + 1) * g.N;
+  if (ctx->gemm_mode == DQMC_GEMM_TENSOR && ctx->qr_mode == DQMC_QR_BLOCKED && g.oz) {
+    ctx->launches += qr_blocked_launches(g.N, g.C, g.oz_batch) - 1;
+    return launch_qr_blocked(g.X, g.nn(), Qt, g.sstride(), Dv, sD, g.Rtil, g.nn(), g.qrb, g.N, g.C,
+                             g.oz, g.oz_batch, ctx->d_status, g.st);
+  }
+  return launch_qrp_cluster(g.X, g.nn(), Qt, g.sstride(), Dv, sD, g.Rtil, g.nn(), g.qrs, g.N, g.C,
+                            ctx->d_status, g.st);
 }
 
 // ---- UDV stack steps ------------------------------------------------------
@@ -332,9 +357,7 @@ int stack_right(dqmc_ctx* ctx, Group& g, int j) {
   DQ_CLASS(ctx, kTStackKron);
   DQ_LAUNCH(ctx, launch_kron_rows<double>(g.RU + (j - 1) * g.nn(), g.X, g.C, a, g.st));
   DQ_CLASS(ctx, kTQR);
-  DQ_LAUNCH(ctx, launch_qrp_cluster(g.X, g.nn(), g.RU + j * g.nn(), g.sstride(), g.RD + j * g.N,
-                                    static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.qrs,
-                                    g.N, g.C, ctx->d_status, g.st));
+  DQ_LAUNCH(ctx, stack_qr(ctx, g, g.RU + j * g.nn(), g.RD + j * g.N));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.balance = 1;  // the rows of T differ in magnitude; Rtil is triangular
@@ -358,9 +381,7 @@ int stack_left(dqmc_ctx* ctx, Group& g, int j) {
   DQ_CLASS(ctx, kTStackKron);
   DQ_LAUNCH(ctx, launch_kron_rows<double>(g.LU + (j + 1) * g.nn(), g.X, g.C, a, g.st));
   DQ_CLASS(ctx, kTQR);
-  DQ_LAUNCH(ctx, launch_qrp_cluster(g.X, g.nn(), g.LU + j * g.nn(), g.sstride(), g.LD + j * g.N,
-                                    static_cast<long long>(g.nc + 1) * g.N, g.Rtil, g.nn(), g.qrs,
-                                    g.N, g.C, ctx->d_status, g.st));
+  DQ_LAUNCH(ctx, stack_qr(ctx, g, g.LU + j * g.nn(), g.LD + j * g.N));
   GemmArgs m = gemm0(g.N);
   m.A = g.Rtil; m.sA = g.nn();
   m.balance = 1;  // the rows of T differ in magnitude; Rtil is triangular
@@ -503,7 +524,7 @@ int up_pass(dqmc_ctx* ctx, Group& g, int measure) {
   ma.ep2l = static_cast<float>(ep2 - static_cast<double>(ma.ep2h));
   ma.accepted = g.acc;
   ma.status = ctx->d_status;
-  ma.cs = ctx->metro_cs;
+  ma.cs = g.tile_metro > 0 ? g.tile_metro : ctx->metro_cs;
   if (ma.cs == 0) {  // all chains of all groups run their Metropolis passes side by side
     ma.cs = 1;
     for (int cs : {4, 2})
@@ -694,6 +715,12 @@ int setup_group(dqmc_ctx* ctx, Group& g) {
   if (static_cast<int>(N) >= kOzakiMinN) {
     g.oz_batch = static_cast<int>(std::min<size_t>(C * S, 256));
     DQ_RET(dev_alloc(ctx, &g.oz, ozaki_scratch_bytes(static_cast<int>(N), g.oz_batch)));
+    DQ_RET(dev_alloc(ctx, &g.qrb.W0, C * NN * 8));
+    DQ_RET(dev_alloc(ctx, &g.qrb.W1, C * NN * 8));
+    DQ_RET(dev_alloc(ctx, &g.qrb.Wt, C * N * 32 * 8));
+    DQ_RET(dev_alloc(ctx, &g.qrb.perm, C * N * sizeof(int)));
+    g.qrb.sW = static_cast<long long>(NN);
+    g.qrb.sWt = static_cast<long long>(N) * 32;
   }
   std::vector<int> cpg = g.cp, cpd = g.cp;
   cpg.push_back(g.L + 1);
@@ -937,6 +964,89 @@ int dqmc_autotune(const dqmc_group* groups, int n_groups, double drift_target, u
   return DQMC_OK;
 }
 
+namespace {
+bool tile_ok(int v, int N) {
+  return v == 0 || ((v == 1 || v == 2 || v == 4 || v == 8 || v == 16) && v <= N);
+}
+}  // namespace
+
+int dqmc_set_tiles(dqmc_ctx* ctx, int group, const dqmc_tiles* t) {
+  if (!ctx || !t || group < 0 || group >= static_cast<int>(ctx->g.size())) return DQMC_ERR_ARG;
+  Group& g = ctx->g[group];
+  if (!tile_ok(t->kron_nv, g.N) || !tile_ok(t->wrap_nv, g.N)) return DQMC_ERR_ARG;
+  if (t->metro_ctas != 0 && t->metro_ctas != 1 && t->metro_ctas != 2 && t->metro_ctas != 4)
+    return DQMC_ERR_ARG;
+  if (t->metro_ctas > 1 && g.N < 4 * t->metro_ctas) return DQMC_ERR_ARG;
+  if (g.tile_kron != t->kron_nv || g.tile_wrap != t->wrap_nv || g.tile_metro != t->metro_ctas)
+    drop_graphs(ctx);
+  g.tile_kron = t->kron_nv;
+  g.tile_wrap = t->wrap_nv;
+  g.tile_metro = t->metro_ctas;
+  return DQMC_OK;
+}
+
+int dqmc_get_tiles(const dqmc_ctx* ctx, int group, dqmc_tiles* out) {
+  if (!ctx || !out || group < 0 || group >= static_cast<int>(ctx->g.size())) return DQMC_ERR_ARG;
+  const Group& g = ctx->g[group];
+  out->kron_nv = kron_nv(g, true);
+  if (g.p.precision == DQMC_FP32)
+    out->wrap_nv = wrap_nv<float>(g);
+  else if (g.p.precision == DQMC_DF32)
+    out->wrap_nv = wrap_nv<df32>(g);
+  else
+    out->wrap_nv = wrap_nv<double>(g);
+  int cs = g.tile_metro > 0 ? g.tile_metro : ctx->metro_cs;
+  if (cs == 0) {
+    cs = 1;
+    for (int c : {4, 2})
+      if (static_cast<long long>(c) * ctx->total <= ctx->nsm && g.N >= 4 * c) {
+        cs = c;
+        break;
+      }
+  }
+  out->metro_ctas = cs;
+  return DQMC_OK;
+}
+
+int dqmc_autotune_tiles(const dqmc_group* groups, int n_groups, uint64_t seed, void* stream,
+                        dqmc_tiles* out) {
+  if (!groups || n_groups < 1 || !out) return DQMC_ERR_ARG;
+  for (int i = 0; i < n_groups; ++i) DQ_RET(validate(groups[i]));
+  // Each class of kernels depends on one tile parameter only (metropolis on
+  // the CTAs per chain, wrap on wrap_nv, the FP64 Kronecker classes on
+  // kron_nv), so one timed sweep per candidate index tunes all three.
+  const int kron_c[3] = {2, 4, 8}, wrap_c[3] = {2, 4, 8}, metro_c[3] = {1, 2, 4};
+  for (int gi = 0; gi < n_groups; ++gi) {
+    dqmc_ctx* pc = nullptr;
+    DQ_RET(dqmc_init(&groups[gi], 1, seed, stream, &pc));
+    const int N = pc->g[0].N;
+    double best[3] = {1e300, 1e300, 1e300};
+    dqmc_tiles pick{0, 0, 0};
+    int rc = dqmc_sweep(pc, 1, 0);  // warm-up (and graph-free first launches)
+    for (int c = 0; c < 3 && rc == DQMC_OK; ++c) {
+      dqmc_tiles t{std::min(kron_c[c], N), std::min(wrap_c[c], N),
+                   N >= 4 * metro_c[c] ? metro_c[c] : 1};
+      rc = dqmc_set_tiles(pc, 0, &t);
+      if (rc == DQMC_OK) rc = dqmc_timing_enable(pc, 1);
+      if (rc == DQMC_OK) rc = dqmc_timing_reset(pc);
+      if (rc == DQMC_OK) rc = dqmc_sweep(pc, 1, 0);
+      double ms[kTNumClasses] = {};
+      if (rc == DQMC_OK && dqmc_timing_read(pc, ms, nullptr, kTNumClasses) < 0) rc = DQMC_ERR_CUDA;
+      if (rc == DQMC_OK) rc = dqmc_timing_enable(pc, 0);
+      if (rc != DQMC_OK) break;
+      const double tm = ms[kTMetropolis], tw = ms[kTWrap], tk = ms[kTStackKron];
+      if (tk < best[0]) { best[0] = tk; pick.kron_nv = t.kron_nv; }
+      if (tw < best[1]) { best[1] = tw; pick.wrap_nv = t.wrap_nv; }
+      if (tm < best[2]) { best[2] = tm; pick.metro_ctas = t.metro_ctas; }
+    }
+    if (rc == DQMC_OK) rc = check_status(pc);
+    dqmc_destroy(pc);
+    DQ_RET(rc);
+    out[gi] = pick;
+  }
+  return DQMC_OK;
+}
+
 int dqmc_use_graphs(dqmc_ctx* ctx, int on) {
   if (!ctx) return DQMC_ERR_ARG;
   ctx->use_graph = on != 0;
@@ -1004,7 +1114,8 @@ int measure_gtau_group(dqmc_ctx* ctx, Group& g, double* dst) {
     // float-pair groups propagate in their working precision (small tiles,
     // latency-bound like the wrap); FP64 and FP32 groups in FP64
     const bool pair = g.p.precision == DQMC_DF32;
-    ga.nv = pair ? std::min(8, g.N) : kron_nv(g, true);
+    ga.nv = pair ? (g.tile_wrap > 0 ? std::min(2 * g.tile_wrap, g.N) : std::min(8, g.N))
+                 : kron_nv(g, true);
     ga.per_chain = g.nc + 1;
     ga.c = g.lam;
     ga.ec = std::exp(g.lam);
@@ -1317,6 +1428,13 @@ int dqmc_set_gemm_mode(dqmc_ctx* ctx, int mode) {
   if (!ctx || (mode != DQMC_GEMM_TENSOR && mode != DQMC_GEMM_FP64)) return DQMC_ERR_ARG;
   if (ctx->gemm_mode != mode) drop_graphs(ctx);
   ctx->gemm_mode = mode;
+  return DQMC_OK;
+}
+
+int dqmc_set_qr_mode(dqmc_ctx* ctx, int mode) {
+  if (!ctx || (mode != DQMC_QR_BLOCKED && mode != DQMC_QR_PIVOTED)) return DQMC_ERR_ARG;
+  if (ctx->qr_mode != mode) drop_graphs(ctx);
+  ctx->qr_mode = mode;
   return DQMC_OK;
 }
 

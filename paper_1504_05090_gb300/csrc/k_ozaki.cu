@@ -42,11 +42,16 @@ namespace {
 constexpr int kS = 8;
 constexpr int kTM = 128, kTN = 64, kTK = 32;
 constexpr int kATile = kTM * kTK * 2;  // bytes of one digit slice of an A chunk (8 KB)
-constexpr int kBTile = kTN * kTK * 2;  // (4 KB)
-constexpr int kStage = kS * (kATile + kBTile);  // 96 KB: all digits of one K chunk
 constexpr int kStages = 2;
-constexpr int kOzSmem = kStages * kStage;
 constexpr long long kWaitLimit = 1LL << 26;
+// Tile width BN (columns of C per CTA) is 64, or 32 for products with at most
+// 32 columns (the panel products of the blocked QR).
+template <int BN>
+struct OzTile {
+  static constexpr int kBTile = BN * kTK * 2;               // one B digit slice of a chunk
+  static constexpr int kStage = kS * (kATile + kBTile);     // all digits of one K chunk
+  static constexpr int kTmemCols = kS * BN;                  // 8 accumulators of BN columns
+};
 
 // Element offset of (slice p, vector v, k) in the tile-blocked digit layout:
 // blocks [p][row tile][K chunk] of R x kTK elements, each block in the
@@ -74,15 +79,15 @@ __device__ __forceinline__ double oz_scale(const double* p, int mode, int i) {
 // Inner-index balance: kexp[k] = unbiased exponent of max_j |op(B)_kj s_k|
 // (s the inner scale when it goes with op(B)), 0 for a zero row.  Integer
 // work only.  One warp per k.
-__global__ void __launch_bounds__(256) k_oz_kexp(const double* Mall, long long sM, int n,
+__global__ void __launch_bounds__(256) k_oz_kexp(const double* Mall, long long sM, int nvec, int K,
                                                 long long sv, long long sk, const double* ksall,
                                                 long long sks, int ks_mode, int* kexpall) {
   const int b = blockIdx.y;
   const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (k >= n) return;
+  if (k >= K) return;
   const double* M = Mall + b * sM;
   int emax = -1;
-  for (int j = lane; j < n; j += 32)
+  for (int j = lane; j < nvec; j += 32)
     emax = max(emax, static_cast<int>((__double_as_longlong(M[j * sv + k * sk]) >> 52) & 0x7FF));
   for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
   if (lane == 0) {
@@ -95,38 +100,62 @@ __global__ void __launch_bounds__(256) k_oz_kexp(const double* Mall, long long s
         if (Es > 0) e += Es - 1023;
       }
     }
-    kexpall[b * static_cast<long long>(n) + k] = e;
+    kexpall[b * static_cast<long long>(K) + k] = e;
   }
 }
 
-// One warp per vector v of the batch entry: element k of vector v is
-// M[v sv + k sk] (times the inner scale of k, times 2^{ksign kexp[k]} when
-// balancing; the power of two only moves the digit alignment, as an integer
-// exponent offset).  Writes the 8 digit slices in the tile-blocked layout
+// One operand of a product for the split kernel: vector v (a row of op(A) or
+// a column of op(B)) has element k at M[v sv + k sk] of batch entry b
+// (M + b sM), times the inner scale of k if it goes with this operand.
+struct OzSplitOp {
+  const double* M;
+  long long sM;
+  int nvec, R;  // vectors, and the row tile they are padded to
+  long long sv, sk;
+  const double* ks;
+  long long sks;
+  int ks_mode;
+  int ksign;  // +1 for op(A), -1 for op(B): sign of the balance exponent
+  __nv_bfloat16* out;
+  long long sOut;
+  int* ex;
+  long long sEx;
+  int blocks;  // blocks of the grid's x dimension that work on this operand
+};
+
+// Both operands of a product in one launch: blocks [0, opA.blocks) split the
+// rows of op(A), the others the columns of op(B).  One warp per vector: the
+// element (times the inner scale, times 2^{ksign kexp[k]} when balancing; the
+// power of two only moves the digit alignment, as an integer exponent
+// offset) is cut into 8 digit slices written in the tile-blocked layout
 // (rows padded to a multiple of R, K to a multiple of the chunk, zero
-// padding) and the scale exponent ex[v].
-__global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long sM, int n, int R,
-                                                 long long sv, long long sk, const double* ksall,
-                                                 long long sks, int ks_mode, const int* kexpall,
-                                                 int ksign, __nv_bfloat16* outall, long long sOut,
-                                                 int* exall, long long sEx) {
-  const int nrt = (n + R - 1) / R, nkc = (n + kTK - 1) / kTK, np = nkc * kTK;
+// padding), with the scale exponent ex[v].
+__global__ void __launch_bounds__(256) k_oz_split(OzSplitOp opA, OzSplitOp opB, int n,
+                                                 const int* kexpall) {
+  const bool isA = static_cast<int>(blockIdx.x) < opA.blocks;
+  const OzSplitOp o = isA ? opA : opB;
+  const int bx = isA ? static_cast<int>(blockIdx.x) : static_cast<int>(blockIdx.x) - opA.blocks;
+  // nvec vectors of length n (the inner dimension K)
+  const int nvec = o.nvec, R = o.R;
+  const long long sv = o.sv, sk = o.sk;
+  const int ks_mode = o.ks_mode;
+  const int nrt = (nvec + R - 1) / R, nkc = (n + kTK - 1) / kTK, np = nkc * kTK;
   const int b = blockIdx.y;
-  const double* M = Mall + b * sM;
+  const double* M = o.M + b * o.sM;
   __shared__ double ksv[kMaxN];
   __shared__ int kev[kMaxN];
-  const double* ks = ksall ? ksall + b * sks : nullptr;
+  const double* ks = o.ks ? o.ks + b * o.sks : nullptr;
   for (int k = threadIdx.x; k < n; k += blockDim.x) {
     ksv[k] = oz_scale(ks, ks_mode, k);
-    kev[k] = kexpall ? ksign * kexpall[b * static_cast<long long>(n) + k] : 0;
+    kev[k] = kexpall ? o.ksign * kexpall[b * static_cast<long long>(n) + k] : 0;
   }
   __syncthreads();
-  const int v = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int v = bx * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (v >= nrt * R) return;
-  __nv_bfloat16* out = outall + b * sOut;
+  __nv_bfloat16* out = o.out + b * o.sOut;
   // Each lane owns 8 consecutive K elements: they are adjacent in the core-matrix
   // layout (np is a multiple of 32), so each digit slice takes one 16-byte store.
-  if (v >= n) {  // padding rows of the last row tile
+  if (v >= nvec) {  // padding rows of the last row tile
     for (int k0 = lane * 8; k0 < np; k0 += 256)
       for (int p = 0; p < kS; ++p)
         *reinterpret_cast<uint4*>(out + oz_offset(p, v, k0, R, nrt, nkc)) = make_uint4(0, 0, 0, 0);
@@ -138,8 +167,8 @@ __global__ void __launch_bounds__(256) k_oz_split(const double* Mall, long long 
     const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
     if (E != 0) emax = max(emax, E - 1023 + kev[k]);
   }
-  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, o));
-  if (lane == 0) exall[b * sEx + v] = emax - 6;
+  for (int q = 16; q > 0; q >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, q));
+  if (lane == 0) o.ex[b * o.sEx + v] = emax - 6;
   for (int k0 = lane * 8; k0 < np; k0 += 256) {
     unsigned long long al[8];
     float sg[8];
@@ -213,14 +242,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, int parity) {
 
 // One thread: bulk-copy all digit slices of K chunk kc (A rows of tile ra, B
 // rows of tile rb) into stage smem; completion is counted on `bar`.
+template <int BN>
 __device__ __forceinline__ void oz_issue_chunk(unsigned char* stage, const __nv_bfloat16* As,
                                                const __nv_bfloat16* Bs, int ra, int rb, int kc,
                                                int nrtA, int nrtB, int nkc, uint64_t* bar) {
+  using Tl = OzTile<BN>;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(static_cast<uint32_t>(kStage)));
+               "r"(static_cast<uint32_t>(Tl::kStage)));
   for (int p = 0; p < kS; ++p) {
     const __nv_bfloat16* ga = As + ((static_cast<size_t>(p) * nrtA + ra) * nkc + kc) * (kTM * kTK);
-    const __nv_bfloat16* gb = Bs + ((static_cast<size_t>(p) * nrtB + rb) * nkc + kc) * (kTN * kTK);
+    const __nv_bfloat16* gb = Bs + ((static_cast<size_t>(p) * nrtB + rb) * nkc + kc) * (BN * kTK);
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(stage + p * kATile)),
@@ -228,12 +259,52 @@ __device__ __forceinline__ void oz_issue_chunk(unsigned char* stage, const __nv_
         : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(stage + kS * kATile + p * kBTile)),
-        "l"(gb), "r"(static_cast<uint32_t>(kBTile)), "r"(smem_u32(bar))
+            smem_u32(stage + kS * kATile + p * Tl::kBTile)),
+        "l"(gb), "r"(static_cast<uint32_t>(Tl::kBTile)), "r"(smem_u32(bar))
         : "memory");
   }
 }
 
+// round(S) 2^e as a double for a signed 128-bit integer S, rounded to nearest
+// with ties to even (IEEE 754), in integer arithmetic only: the position of
+// the leading bit gives the exponent, the 52 bits below it the significand,
+// and the bits shifted out decide the rounding.  ok = false when the result
+// would be subnormal or overflow (the caller then takes the FP64 route).
+__device__ __forceinline__ double i128_to_double(__int128 S, int e, bool& ok) {
+  ok = true;
+  if (S == 0) return 0.0;
+  const bool neg = S < 0;
+  const unsigned __int128 mag = neg ? static_cast<unsigned __int128>(-S) : static_cast<unsigned __int128>(S);
+  const unsigned long long mh = static_cast<unsigned long long>(mag >> 64);
+  const unsigned long long ml = static_cast<unsigned long long>(mag);
+  int b = mh ? 127 - __clzll(static_cast<long long>(mh)) : 63 - __clzll(static_cast<long long>(ml));
+  unsigned long long m;
+  if (b <= 52) {
+    m = ml << (52 - b);
+  } else {
+    const int sh = b - 52;  // 1 .. 75
+    const unsigned __int128 q = mag >> sh;
+    m = static_cast<unsigned long long>(q);
+    const unsigned __int128 rem = mag - (q << sh);
+    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m == (1ull << 53)) {
+        m >>= 1;
+        ++b;
+      }
+    }
+  }
+  const int E = b + e + 1023;
+  ok = E > 0 && E < 2047;
+  const unsigned long long bits = (static_cast<unsigned long long>(neg) << 63) |
+                                  (static_cast<unsigned long long>(E) << 52) |
+                                  (m & ((1ull << 52) - 1));
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// C (M x Nc, leading dimension ldc) = alpha diag(rs) [digit product] diag(cs)
+// + beta C for each batch entry; K is the inner dimension.
 struct OzMmaArgs {
   const __nv_bfloat16* As;
   long long sAs;
@@ -245,7 +316,7 @@ struct OzMmaArgs {
   long long sExB;
   double* C;
   long long sC;
-  int n;
+  int M, Nc, K, ldc;
   const double* rs;
   long long srs;
   int rs_mode;
@@ -256,27 +327,33 @@ struct OzMmaArgs {
   int* status;
 };
 
+template <int BN>
 __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
+  using Tl = OzTile<BN>;
   extern __shared__ __align__(1024) unsigned char oz_sm[];
   __shared__ uint64_t full[kStages], mmad[kStages];
   __shared__ uint32_t tmem_sh;
   __shared__ int fail_sh;
-  __shared__ double colf[kTN];  // cs_j 2^{f_j - 21} of this CTA's columns
+  __shared__ double colf[BN];  // cs_j 2^{f_j - 21} of this CTA's columns
+  __shared__ int colx[BN];     // f_j of this CTA's columns
   const int b = blockIdx.z;
-  const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * kTN;
+  const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * BN;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = a.n;
-  const int nrtA = (n + kTM - 1) / kTM, nrtB = (n + kTN - 1) / kTN, nkc = (n + kTK - 1) / kTK;
+  const int M = a.M, Nc = a.Nc;
+  const int nrtA = (M + kTM - 1) / kTM, nrtB = (Nc + BN - 1) / BN, nkc = (a.K + kTK - 1) / kTK;
   const __nv_bfloat16* As = a.As + b * a.sAs;
   const __nv_bfloat16* Bs = a.Bs + b * a.sBs;
-  if (threadIdx.x >= 64) {
-    const int q = threadIdx.x - 64, j = j0 + q;
-    colf[q] = (j < n) ? oz_scale(a.cs ? a.cs + b * a.scs : nullptr, a.cs_mode, j) *
-                            ldexp(1.0, a.exB[b * a.sExB + j] - 21)
-                      : 0.0;
+  if (threadIdx.x >= 128 - BN) {
+    const int q = threadIdx.x - (128 - BN), j = j0 + q;
+    colf[q] = (j < Nc) ? oz_scale(a.cs ? a.cs + b * a.scs : nullptr, a.cs_mode, j) *
+                             ldexp(1.0, a.exB[b * a.sExB + j] - 21)
+                       : 0.0;
+    colx[q] = (j < Nc) ? a.exB[b * a.sExB + j] : 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(&tmem_sh)));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_sh)),
+                 "n"(Tl::kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (threadIdx.x == 0) {
@@ -292,7 +369,7 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tbase = tmem_sh;
   // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N, M.
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTN >> 3) << 17) | ((kTM >> 4) << 24);
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((BN >> 3) << 17) | ((kTM >> 4) << 24);
   if (threadIdx.x == 0) {
     // Producer and MMA issuer.  Chunk c sits in stage c & 1.  After the MMAs
     // of chunk c are queued, the MMAs of chunk c - 1 (queued earlier, so done
@@ -300,7 +377,7 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
     // tensor pipe works on chunk c.
     int pend_load[kStages] = {-1, -1};  // parity of an outstanding load per stage
     int committed = -1;                 // last chunk whose MMAs were committed
-    oz_issue_chunk(oz_sm, As, Bs, blockIdx.y, blockIdx.x, 0, nrtA, nrtB, nkc, &full[0]);
+    oz_issue_chunk<BN>(oz_sm, As, Bs, blockIdx.y, blockIdx.x, 0, nrtA, nrtB, nkc, &full[0]);
     pend_load[0] = 0;
     for (int c = 0; c < nkc; ++c) {
       const int st = c & 1;
@@ -310,18 +387,18 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
       }
       pend_load[st] = -1;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      unsigned char* smA = oz_sm + st * kStage;
+      unsigned char* smA = oz_sm + st * Tl::kStage;
       unsigned char* smB = smA + kS * kATile;
       for (int d = 0; d < kS; ++d)
         for (int p = 0; p <= d; ++p) {
           const int q = d - p;
           for (int ks = 0; ks < kTK / 16; ++ks) {
             const uint64_t ad = oz_desc(smem_u32(smA + p * kATile + ks * 256));
-            const uint64_t bd = oz_desc(smem_u32(smB + q * kBTile + ks * 256));
+            const uint64_t bd = oz_desc(smem_u32(smB + q * Tl::kBTile + ks * 256));
             const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
             asm volatile(
                 "{\n .reg .pred pa;\n setp.ne.u32 pa, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tbase + d * kTN),
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tbase + d * BN),
                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
           }
         }
@@ -334,8 +411,8 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
           fail_sh = 1;
           break;
         }
-        oz_issue_chunk(oz_sm + so * kStage, As, Bs, blockIdx.y, blockIdx.x, c + 1, nrtA, nrtB, nkc,
-                       &full[so]);
+        oz_issue_chunk<BN>(oz_sm + so * Tl::kStage, As, Bs, blockIdx.y, blockIdx.x, c + 1, nrtA,
+                           nrtB, nkc, &full[so]);
         pend_load[so] = ((c + 1) >> 1) & 1;
       }
     }
@@ -357,22 +434,29 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // Recombination.  Every accumulator holds an integer P_d (a sum of digit
-    // products); sum_d P_d 2^{-7d} = 2^{-21} (hi + 2^{-28} lo) with the exact
-    // 64-bit integers hi = sum_{d<4} P_d 2^{7(3-d)} and lo = sum_{d>=4} P_d
-    // 2^{7(7-d)} (both below 2^47, so exact in FP64): two conversions and one
-    // FMA in FP64 per element, the scales from per-row / per-column factors.
+    // products); sum_d P_d 2^{-7d} = 2^{-49} S with the exact 128-bit integer
+    // S = 2^28 hi + lo, hi = sum_{d<4} P_d 2^{7(3-d)}, lo = sum_{d>=4} P_d
+    // 2^{7(7-d)}.  S is rounded to a double once, in integer arithmetic.
+    // Without row and column scales (alpha = +-1) the powers of two 2^{e_i + f_j}
+    // go into the exponent as well, which leaves one FP64 operation per
+    // element (the accumulation into C when beta != 0); otherwise the scales
+    // are two FP64 products.  Both give the value fma(lo, 2^-28, hi) 2^{-21}
+    // times the scales, rounded once, as an FP64 evaluation would.
     const int i = i0 + warp * 32 + lane;
-    const bool row_ok = i < n;
+    const bool row_ok = i < M;
     const double rowf =
         row_ok ? a.alpha * oz_scale(a.rs ? a.rs + b * a.srs : nullptr, a.rs_mode, i) *
                      ldexp(1.0, a.exA[b * a.sExA + i])
                : 0.0;
+    const bool pow2 = (a.rs == nullptr || a.rs_mode == 0) && (a.cs == nullptr || a.cs_mode == 0) &&
+                      (a.alpha == 1.0 || a.alpha == -1.0);
+    const int rowx = row_ok ? a.exA[b * a.sExA + i] : 0;
     double* C = a.C + b * a.sC;
-    for (int c = 0; c < kTN / 16; ++c) {
+    for (int c = 0; c < BN / 16; ++c) {
       uint32_t v[kS][16];
 #pragma unroll
       for (int d = 0; d < kS; ++d) {
-        const uint32_t ta = tbase + (static_cast<uint32_t>(warp * 32) << 16) + d * kTN + c * 16;
+        const uint32_t ta = tbase + (static_cast<uint32_t>(warp * 32) << 16) + d * BN + c * 16;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
@@ -385,7 +469,7 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int jj = c * 16 + q, j = j0 + jj;
-          if (j < n) {
+          if (j < Nc) {
             long long hi = 0, lo = 0;
 #pragma unroll
             for (int d = 0; d < 4; ++d)
@@ -393,9 +477,20 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
 #pragma unroll
             for (int d = 4; d < kS; ++d)
               lo += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (7 - d));
-            const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
-            double val = (sum * rowf) * colf[jj];
-            const size_t o = static_cast<size_t>(i) * n + j;
+            __int128 S = (static_cast<__int128>(hi) << 28) + lo;
+            bool ok;
+            double val;
+            if (pow2) {
+              if (a.alpha < 0.0) S = -S;
+              val = i128_to_double(S, rowx + colx[jj] - 49, ok);
+            } else {
+              val = i128_to_double(S, -28, ok) * rowf * colf[jj];
+            }
+            if (!ok) {  // subnormal or overflowing intermediate: the FP64 route
+              const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
+              val = (sum * rowf) * colf[jj];
+            }
+            const size_t o = static_cast<size_t>(i) * a.ldc + j;
             if (a.beta != 0.0) val = fma(a.beta, C[o], val);
             C[o] = val;
           }
@@ -405,71 +500,102 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "n"(Tl::kTmemCols));
 }
 
-}  // namespace
-
-static size_t oz_slice_elems(int n, int R) {
-  const size_t nrt = (n + R - 1) / R, nkc = (n + kTK - 1) / kTK;
+size_t oz_slice_elems(int nvec, int K, int R) {
+  const size_t nrt = (nvec + R - 1) / R, nkc = (K + kTK - 1) / kTK;
   return static_cast<size_t>(kS) * nrt * R * nkc * kTK;
 }
 
-size_t ozaki_scratch_bytes(int n, int max_batch) {
-  return static_cast<size_t>(max_batch) *
-             ((oz_slice_elems(n, kTM) + oz_slice_elems(n, kTN)) * 2 + 3ull * n * sizeof(int)) +
-         1024;
-}
-
-cudaError_t launch_gemm_ozaki(const GemmArgs& g, int batch, void* scratch, int max_batch,
-                              int* status, cudaStream_t st) {
-  const int n = g.n;
-  if (n <= 0 || batch <= 0) return cudaSuccess;
-  const long long slA = static_cast<long long>(oz_slice_elems(n, kTM));
-  const long long slB = static_cast<long long>(oz_slice_elems(n, kTN));
+template <int BN>
+cudaError_t oz_run(const OzProduct& g, int batch, void* scratch, int max_batch, int* status,
+                   cudaStream_t st) {
+  using Tl = OzTile<BN>;
+  const int M = g.M, Nc = g.Nc, K = g.K;
+  const long long slA = static_cast<long long>(oz_slice_elems(M, K, kTM));
+  const long long slB = static_cast<long long>(oz_slice_elems(Nc, K, BN));
   __nv_bfloat16* As = static_cast<__nv_bfloat16*>(scratch);
   __nv_bfloat16* Bs = As + slA * max_batch;
   int* exA = reinterpret_cast<int*>(Bs + slB * max_batch);
-  int* exB = exA + static_cast<long long>(n) * max_batch;
-  int* kexp = exB + static_cast<long long>(n) * max_batch;
-  cudaError_t e = cudaFuncSetAttribute(k_oz_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+  int* exB = exA + static_cast<long long>(M) * max_batch;
+  int* kexp = exB + static_cast<long long>(Nc) * max_batch;
+  const int nkc = (K + kTK - 1) / kTK;
+  const int stages = nkc > 1 ? kStages : 1;  // a single K chunk needs one stage
+  const int smem = stages * Tl::kStage;
+  cudaError_t e = cudaFuncSetAttribute(k_oz_mma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStages * Tl::kStage);
   if (e != cudaSuccess) return e;
-  const int rowsA = (n + kTM - 1) / kTM * kTM, rowsB = (n + kTN - 1) / kTN * kTN;
+  const int rowsA = (M + kTM - 1) / kTM * kTM, rowsB = (Nc + BN - 1) / BN * BN;
   for (int b0 = 0; b0 < batch; b0 += max_batch) {
     const int nb = std::min(max_batch, batch - b0);
     // The inner scale goes with op(A) (ks_on_b = 0) or with op(B).
     const double* ks = g.ks ? g.ks + b0 * g.sks : nullptr;
     const int ks_mode = g.ks ? g.ks_mode : 0;
     const bool on_b = g.ks_on_b != 0;
-    // op(B) element (k, j): tB = 0 -> B[k][j]; tB = 1 -> B[j][k]
-    const long long bsv = g.tB ? n : 1, bsk = g.tB ? 1 : n;
     if (g.balance)
-      k_oz_kexp<<<dim3((n + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, n, bsv, bsk,
-                                                       on_b ? ks : nullptr, g.sks,
+      k_oz_kexp<<<dim3((K + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, Nc, K, g.b_sv,
+                                                       g.b_sk, on_b ? ks : nullptr, g.sks,
                                                        on_b ? ks_mode : 0, kexp);
     const int* kx = g.balance ? kexp : nullptr;
-    // rows of op(A) [diag(ks)]: tA = 0 -> A[i][k]; tA = 1 -> A[k][i]
-    k_oz_split<<<dim3((rowsA + 7) / 8, nb), 256, 0, st>>>(
-        g.A + b0 * g.sA, g.sA, n, kTM, g.tA ? 1 : n, g.tA ? n : 1, on_b ? nullptr : ks, g.sks,
-        on_b ? 0 : ks_mode, kx, 1, As, slA, exA, n);
-    // columns of [diag(ks)] op(B)
-    k_oz_split<<<dim3((rowsB + 7) / 8, nb), 256, 0, st>>>(
-        g.B + b0 * g.sB, g.sB, n, kTN, bsv, bsk, on_b ? ks : nullptr, g.sks, on_b ? ks_mode : 0,
-        kx, -1, Bs, slB, exB, n);
+    // rows of op(A) [diag(ks)] and columns of [diag(ks)] op(B), one launch
+    OzSplitOp oa{g.A + b0 * g.sA, g.sA, M, kTM, g.a_sv, g.a_sk, on_b ? nullptr : ks, g.sks,
+                 on_b ? 0 : ks_mode, 1, As, slA, exA, M, (rowsA + 7) / 8};
+    OzSplitOp ob{g.B + b0 * g.sB, g.sB, Nc, BN, g.b_sv, g.b_sk, on_b ? ks : nullptr, g.sks,
+                 on_b ? ks_mode : 0, -1, Bs, slB, exB, Nc, (rowsB + 7) / 8};
+    k_oz_split<<<dim3(oa.blocks + ob.blocks, nb), 256, 0, st>>>(oa, ob, K, kx);
     OzMmaArgs m;
-    m.As = As; m.sAs = slA; m.exA = exA; m.sExA = n;
-    m.Bs = Bs; m.sBs = slB; m.exB = exB; m.sExB = n;
+    m.As = As; m.sAs = slA; m.exA = exA; m.sExA = M;
+    m.Bs = Bs; m.sBs = slB; m.exB = exB; m.sExB = Nc;
     m.C = g.C + b0 * g.sC; m.sC = g.sC;
-    m.n = n;
+    m.M = M; m.Nc = Nc; m.K = K; m.ldc = g.ldc;
     m.rs = g.rs ? g.rs + b0 * g.srs : nullptr; m.srs = g.srs; m.rs_mode = g.rs ? g.rs_mode : 0;
     m.cs = g.cs ? g.cs + b0 * g.scs : nullptr; m.scs = g.scs; m.cs_mode = g.cs ? g.cs_mode : 0;
     m.alpha = g.alpha; m.beta = g.beta;
     m.status = status;
-    k_oz_mma<<<dim3((n + kTN - 1) / kTN, (n + kTM - 1) / kTM, nb), 128, kOzSmem, st>>>(m);
+    k_oz_mma<BN><<<dim3((Nc + BN - 1) / BN, (M + kTM - 1) / kTM, nb), 128, smem, st>>>(m);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace
+
+size_t ozaki_scratch_bytes(int n, int max_batch) {
+  return static_cast<size_t>(max_batch) *
+             ((oz_slice_elems(n, n, kTM) + oz_slice_elems(n, n, kTN)) * 2 + 3ull * n * sizeof(int)) +
+         1024;
+}
+
+cudaError_t launch_ozaki_product(const OzProduct& g, int batch, void* scratch, int max_batch,
+                                 int* status, cudaStream_t st) {
+  if (g.M <= 0 || g.Nc <= 0 || g.K <= 0 || batch <= 0) return cudaSuccess;
+  if (g.K > kMaxN) return cudaErrorInvalidValue;  // the split kernel stages K scales in smem
+  if (g.Nc <= 32) return oz_run<32>(g, batch, scratch, max_batch, status, st);
+  return oz_run<64>(g, batch, scratch, max_batch, status, st);
+}
+
+cudaError_t launch_gemm_ozaki(const GemmArgs& g, int batch, void* scratch, int max_batch,
+                              int* status, cudaStream_t st) {
+  const int n = g.n;
+  OzProduct p{};
+  p.M = p.Nc = p.K = n;
+  p.A = g.A; p.sA = g.sA;
+  // rows of op(A): tA = 0 -> A[i][k]; tA = 1 -> A[k][i]
+  p.a_sv = g.tA ? 1 : n; p.a_sk = g.tA ? n : 1;
+  p.B = g.B; p.sB = g.sB;
+  // op(B) element (k, j): tB = 0 -> B[k][j]; tB = 1 -> B[j][k]
+  p.b_sv = g.tB ? n : 1; p.b_sk = g.tB ? 1 : n;
+  p.C = g.C; p.sC = g.sC; p.ldc = n;
+  p.rs = g.rs; p.srs = g.srs; p.rs_mode = g.rs_mode;
+  p.ks = g.ks; p.sks = g.sks; p.ks_mode = g.ks_mode; p.ks_on_b = g.ks_on_b;
+  p.balance = g.balance;
+  p.cs = g.cs; p.scs = g.scs; p.cs_mode = g.cs_mode;
+  p.alpha = g.alpha; p.beta = g.beta;
+  return launch_ozaki_product(p, batch, scratch, max_batch, status, st);
 }
 
 }  // namespace dqmc

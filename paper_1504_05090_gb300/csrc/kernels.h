@@ -102,6 +102,24 @@ cudaError_t launch_gemm(const GemmArgs& a, int batch, cudaStream_t st);
 size_t ozaki_scratch_bytes(int n, int max_batch);
 cudaError_t launch_gemm_ozaki(const GemmArgs& a, int batch, void* scratch, int max_batch,
                               int* status, cudaStream_t st);
+// General form of the same tensor-core product: for each batch entry b,
+//   C[i*ldc + j] = alpha rs_i sum_k opA(i,k) ks_k opB(k,j) cs_j + beta C[i*ldc + j]
+// with opA(i,k) = A[i a_sv + k a_sk] (i < M, k < K) and opB(k,j) = B[j b_sv + k b_sk]
+// (j < Nc), batch strides sA, sB, sC; scale modes and balance as in GemmArgs.
+// M, Nc, K <= n of the scratch (ozaki_scratch_bytes(n, max_batch)); K <= 256.
+struct OzProduct {
+  int M, Nc, K;
+  const double* A; long long sA, a_sv, a_sk;
+  const double* B; long long sB, b_sv, b_sk;
+  double* C; long long sC; int ldc;
+  const double* rs; long long srs; int rs_mode;
+  const double* ks; long long sks; int ks_mode; int ks_on_b;
+  int balance;
+  const double* cs; long long scs; int cs_mode;
+  double alpha, beta;
+};
+cudaError_t launch_ozaki_product(const OzProduct& p, int batch, void* scratch, int max_batch,
+                                 int* status, cudaStream_t st);
 // Householder QR with column pivoting of X^T stored row-major (row c = column
 // c of X).  Outputs Q^T (row c = column c of Q), D = |diag R| and
 // Rtil = D^{-1} R P^T with X = Q diag(D) Rtil.  X is overwritten.
@@ -115,6 +133,23 @@ cudaError_t launch_gj_inverse(double* A, long long sA, int n, int batch, double*
 cudaError_t launch_qrp_cluster(double* Xt, long long sX, double* Qt, long long sQ, double* D,
                                long long sD, double* Rtil, long long sR, double* vnorm, int n,
                                int batch, int* status, cudaStream_t st);
+// Blocked Householder QR with panel-wise pivoting (k_qr_blocked.cu): the same
+// inputs and outputs as launch_qrp_cluster (X^T in, Q^T, D, Rtil out); the
+// remaining columns are sorted by norm at every panel of 32 and pivoted within
+// it, and the trailing updates and the accumulation of Q run on the
+// tensor-core products (oz: scratch of ozaki_scratch_bytes(n, oz_batch)).
+// X and Rtil double as workspace; QrbWork adds two n x n buffers W0, W1, Wt
+// (n x 32) and perm (n ints) per matrix.
+struct QrbWork {
+  double* W0; double* W1; long long sW;
+  double* Wt; long long sWt;
+  int* perm;
+};
+cudaError_t launch_qr_blocked(double* Xt, long long sX, double* Qt, long long sQ, double* D,
+                              long long sD, double* Rtil, long long sR, const QrbWork& wk, int n,
+                              int batch, void* oz, int oz_batch, int* status, cudaStream_t st);
+// Kernel launches of one launch_qr_blocked call.
+int qr_blocked_launches(int n, int batch, int oz_batch);
 // Gauss-Jordan: A (overwritten) -> Ainv, out of place; logabs may be null.
 // pair: eliminate in float pairs (A is converted in place first; Ainv and
 // logabs stay FP64).

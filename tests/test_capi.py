@@ -191,3 +191,13 @@ def test_logweight_rejects_parameters_other_than_the_contexts():
     FakeSim.groups.append(pkg.Group(Lx=4, Ly=4, t=0.25, U=3.0, dtau=0.125))
     with pytest.raises(ValueError):  # groups with different lambda: no single (t, lambda)
         pkg.LogWeight.check_parameters(FakeSim, 0.25, lam)
+
+
+def test_set_tiles_argument_checks_without_gpu(libpath):
+    from paper_1504_05090_gb300 import _lib
+    lib = _lib.load(libpath)
+    t = _lib.DqmcTiles(4, 4, 2)
+    assert lib.dqmc_set_tiles(None, 0, ctypes.byref(t)) == -1
+    out = _lib.DqmcTiles()
+    assert lib.dqmc_get_tiles(None, 0, ctypes.byref(out)) == -1
+    assert lib.dqmc_autotune_tiles(None, 1, 0, None, ctypes.byref(out)) == -1
