@@ -319,7 +319,8 @@ GemmArgs gemm0(int n) {
 // N >= kOzakiMinN unless the context asks for the FP64 pipe.
 cudaError_t gemm(dqmc_ctx* ctx, Group& g, const GemmArgs& m, int batch) {
   if (ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz) {
-    // the split kernel (plus the balance pass) besides the MMA kernel, per chunk
+    // the split and the MMA kernel (plus the balance pass) per chunk of the
+    // batch (the square products take the split path)
     const int chunks = (batch + g.oz_batch - 1) / g.oz_batch;
     ctx->launches += static_cast<long long>(chunks) * (m.balance ? 3 : 2) - 1;
     return launch_gemm_ozaki(m, batch, g.oz, g.oz_batch, ctx->d_status, g.st);

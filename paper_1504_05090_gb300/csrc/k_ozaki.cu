@@ -265,42 +265,14 @@ __device__ __forceinline__ void oz_issue_chunk(unsigned char* stage, const __nv_
   }
 }
 
-// round(S) 2^e as a double for a signed 128-bit integer S, rounded to nearest
-// with ties to even (IEEE 754), in integer arithmetic only: the position of
-// the leading bit gives the exponent, the 52 bits below it the significand,
-// and the bits shifted out decide the rounding.  ok = false when the result
-// would be subnormal or overflow (the caller then takes the FP64 route).
-__device__ __forceinline__ double i128_to_double(__int128 S, int e, bool& ok) {
-  ok = true;
-  if (S == 0) return 0.0;
-  const bool neg = S < 0;
-  const unsigned __int128 mag = neg ? static_cast<unsigned __int128>(-S) : static_cast<unsigned __int128>(S);
-  const unsigned long long mh = static_cast<unsigned long long>(mag >> 64);
-  const unsigned long long ml = static_cast<unsigned long long>(mag);
-  int b = mh ? 127 - __clzll(static_cast<long long>(mh)) : 63 - __clzll(static_cast<long long>(ml));
-  unsigned long long m;
-  if (b <= 52) {
-    m = ml << (52 - b);
-  } else {
-    const int sh = b - 52;  // 1 .. 75
-    const unsigned __int128 q = mag >> sh;
-    m = static_cast<unsigned long long>(q);
-    const unsigned __int128 rem = mag - (q << sh);
-    const unsigned __int128 half = static_cast<unsigned __int128>(1) << (sh - 1);
-    if (rem > half || (rem == half && (m & 1ull))) {
-      ++m;
-      if (m == (1ull << 53)) {
-        m >>= 1;
-        ++b;
-      }
-    }
-  }
-  const int E = b + e + 1023;
-  ok = E > 0 && E < 2047;
-  const unsigned long long bits = (static_cast<unsigned long long>(neg) << 63) |
-                                  (static_cast<unsigned long long>(E) << 52) |
-                                  (m & ((1ull << 52) - 1));
-  return __longlong_as_double(static_cast<long long>(bits));
+// d 2^e for a normal double d by adding e to its exponent field (integer
+// arithmetic); ok = false for zero, subnormal or overflowing results.
+__device__ __forceinline__ double scale_pow2(double d, int e, bool& ok) {
+  const long long bits = __double_as_longlong(d);
+  const int E = static_cast<int>((bits >> 52) & 0x7FF);
+  const int E2 = E + e;
+  ok = E != 0 && E != 0x7FF && E2 > 0 && E2 < 2047;
+  return __longlong_as_double((bits & ~(0x7FFLL << 52)) | (static_cast<long long>(E2 & 0x7FF) << 52));
 }
 
 // C (M x Nc, leading dimension ldc) = alpha diag(rs) [digit product] diag(cs)
@@ -430,18 +402,18 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
     const int last = nkc - 1;
     ok = mbar_wait(&mmad[last & 1], (last >> 1) & 1);
   }
+  ok = __syncthreads_and(ok) != 0;  // one decision for the block (the epilogue has a barrier)
   if (!ok && threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // Recombination.  Every accumulator holds an integer P_d (a sum of digit
-    // products); sum_d P_d 2^{-7d} = 2^{-49} S with the exact 128-bit integer
-    // S = 2^28 hi + lo, hi = sum_{d<4} P_d 2^{7(3-d)}, lo = sum_{d>=4} P_d
-    // 2^{7(7-d)}.  S is rounded to a double once, in integer arithmetic.
-    // Without row and column scales (alpha = +-1) the powers of two 2^{e_i + f_j}
-    // go into the exponent as well, which leaves one FP64 operation per
-    // element (the accumulation into C when beta != 0); otherwise the scales
-    // are two FP64 products.  Both give the value fma(lo, 2^-28, hi) 2^{-21}
-    // times the scales, rounded once, as an FP64 evaluation would.
+    // products); sum_d P_d 2^{-7d} = 2^{-21} (hi + 2^{-28} lo) with the exact
+    // 64-bit integers hi = sum_{d<4} P_d 2^{7(3-d)} and lo = sum_{d>=4} P_d
+    // 2^{7(7-d)} (both below 2^47, so exact in FP64): two conversions and one
+    // FMA round the sum once.  Without row and column scales (alpha = +-1)
+    // the power of two 2^{e_i + f_j - 21} and the sign go into the exponent
+    // and sign fields as integers; otherwise the scales are two FP64
+    // products.
     const int i = i0 + warp * 32 + lane;
     const bool row_ok = i < M;
     const double rowf =
@@ -477,19 +449,11 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
 #pragma unroll
             for (int d = 4; d < kS; ++d)
               lo += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (7 - d));
-            __int128 S = (static_cast<__int128>(hi) << 28) + lo;
-            bool ok;
+            const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
             double val;
-            if (pow2) {
-              if (a.alpha < 0.0) S = -S;
-              val = i128_to_double(S, rowx + colx[jj] - 49, ok);
-            } else {
-              val = i128_to_double(S, -28, ok) * rowf * colf[jj];
-            }
-            if (!ok) {  // subnormal or overflowing intermediate: the FP64 route
-              const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
-              val = (sum * rowf) * colf[jj];
-            }
+            bool ok2 = false;
+            if (pow2) val = scale_pow2(a.alpha < 0.0 ? -sum : sum, rowx + colx[jj] - 21, ok2);
+            if (!ok2) val = (sum * rowf) * colf[jj];
             const size_t o = static_cast<size_t>(i) * a.ldc + j;
             if (a.beta != 0.0) val = fma(a.beta, C[o], val);
             C[o] = val;
@@ -503,6 +467,432 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
                  "n"(Tl::kTmemCols));
+}
+
+// ---------------------------------------------------------------------------
+// Fused product: the digit slices are cut by the CTA itself, straight into
+// the shared-memory stage the tensor cores read, so no slice makes a round
+// trip through global memory and no split kernel runs.  256 threads: all of
+// them split (the 128 rows of op(A) and BN columns of op(B) of the tile, one
+// K chunk of 32 at a time, two stages), thread 0 also issues the MMAs of a
+// chunk once every thread has arrived on the stage's `full` barrier (each
+// after a proxy fence that makes its shared-memory writes visible to the
+// tensor cores); splitting chunk c + 1 overlaps the MMAs of chunk c.
+// Before the K loop the CTA finds the exponent of every row of op(A) and
+// column of op(B) of its tile over the whole K range (the digit alignment).
+// Memory access follows the operand's layout: a vector contiguous along k is
+// read by lanes along k, otherwise lanes run along the vectors.
+// ---------------------------------------------------------------------------
+struct OzFusedArgs {
+  const double* A; long long sA, a_sv, a_sk;
+  const double* B; long long sB, b_sv, b_sk;
+  int M, Nc, K;
+  const double* ks; long long sks; int ks_mode, ks_on_b;
+  const int* kexp;  // balance exponents [batch][K] or null
+  double* C; long long sC; int ldc;
+  const double* rs; long long srs; int rs_mode;
+  const double* cs; long long scs; int cs_mode;
+  double alpha, beta;
+  int* status;
+};
+
+constexpr int kFT = 256;  // threads of the fused kernel
+
+// Exponent (unbiased, plus the balance offset) of the largest element of
+// vector v of an operand over k < K; -100000 for a zero vector.
+__device__ __forceinline__ int oz_vec_emax_lanes_k(const double* M, long long sv, long long sk, int v,
+                                                  int K, const double* kss, const int* kev,
+                                                  int ksign, bool scaled, int lane) {
+  int emax = -100000;
+  for (int k = lane; k < K; k += 32) {
+    double x = M[v * sv + k * sk];
+    if (scaled) x *= kss[k];
+    const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
+    if (E != 0) emax = max(emax, E - 1023 + ksign * kev[k]);
+  }
+  for (int q = 16; q > 0; q >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, q));
+  return emax;
+}
+
+// The 8 digit slices of elements k0 .. k0 + 7 of vector v (already scaled;
+// kv = balance exponent offsets; aligned to the vector's exponent emax), one
+// 16-byte unit per slice in the core-matrix layout of a stage operand with R
+// rows.  The aligned 53-bit magnitude is cut with 32-bit bit-field extracts
+// (digit p = bits 46 - 7p .. 52 - 7p; the last digit is bits 0 .. 3 moved up
+// by 3); a digit d becomes the float +-d through the exponent of 2^23
+// (bits 0x4B000000 | d are 2^23 + d) and one FMA with the sign, and two floats
+// are packed to a BF16 pair (exact: d < 128).
+__device__ __forceinline__ uint32_t oz_bfe(uint32_t x, int pos) {
+  uint32_t d;
+  asm("bfe.u32 %0, %1, %2, 7;" : "=r"(d) : "r"(x), "r"(pos));
+  return d;
+}
+
+__device__ __forceinline__ void oz_split_unit(const double (&x)[8], const int (&kv)[8], int emax,
+                                              unsigned char* op, int R, int v, int kg) {
+  uint32_t h[8], l[8];
+  float sg[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const long long bits = __double_as_longlong(x[e]);
+    const int E = static_cast<int>((bits >> 52) & 0x7FF);
+    unsigned long long al = 0ULL;
+    if (E != 0) {  // zero and subnormal inputs contribute zero digits
+      const unsigned long long mant =
+          (static_cast<unsigned long long>(bits) & ((1ULL << 52) - 1)) | (1ULL << 52);
+      const int sh = emax - (E - 1023 + kv[e]);
+      al = (sh < 64) ? (mant >> sh) : 0ULL;
+    }
+    h[e] = static_cast<uint32_t>(al >> 32);
+    l[e] = static_cast<uint32_t>(al);
+    sg[e] = (bits < 0) ? -1.0f : 1.0f;
+  }
+  // element offset of (v, 8 kg) within one slice: core matrices of 8 rows x 8 k
+  const int off = (v >> 3) * (kTK / 8 * 64) + kg * 64 + (v & 7) * 8;
+  constexpr float kTwo23 = 8388608.0f;
+#pragma unroll
+  for (int p = 0; p < kS; ++p) {
+    uint32_t w[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      float f[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        uint32_t d;
+        if (p < 3)
+          d = oz_bfe(h[e + q], 14 - 7 * p);
+        else if (p == 3)
+          d = l[e + q] >> 25;
+        else if (p < 7)
+          d = oz_bfe(l[e + q], 46 - 7 * p);
+        else
+          d = (l[e + q] & 15u) << 3;
+        f[q] = fmaf(__uint_as_float(0x4B000000u | d), sg[e + q], -kTwo23 * sg[e + q]);
+      }
+      const __nv_bfloat162 hb = __floats2bfloat162_rn(f[0], f[1]);
+      w[e >> 1] = *reinterpret_cast<const uint32_t*>(&hb);
+    }
+    *reinterpret_cast<uint4*>(op + (static_cast<size_t>(p) * R * kTK + off) * 2) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// One operand of the fused product as the split of a K chunk sees it.
+struct OzOperand {
+  const double* M;
+  long long sv, sk;
+  int v0, nvec, R, ksign;
+  bool scaled;
+  const int* ex;
+  unsigned char* op;  // the operand's slices in the stage
+};
+
+// Unit u of a K chunk of one operand: vector v and k group kg.  A vector
+// contiguous along k gives 8 consecutive vectors x 4 k groups per 32 units
+// (conflict-free 16-byte stores), otherwise lanes run along the vectors.
+__device__ __forceinline__ void oz_unit_coords(const OzOperand& o, int u, int& v, int& kg) {
+  if (o.sk == 1) {
+    v = (u & 7) + 8 * (u >> 5);
+    kg = (u >> 3) & 3;
+  } else {
+    kg = u / o.R;
+    v = u - kg * o.R;
+  }
+}
+
+// Split K chunk kc of both operands into the stage: every thread takes up to
+// kUnitsPerThread units, loads all their elements first (independent loads
+// in flight), then cuts them.
+constexpr int kUnitsPerThread = 3;
+__device__ __forceinline__ void oz_split_chunk2(const OzOperand& oa, const OzOperand& ob, int K,
+                                                int kc, const double* kss, const int* kev) {
+  const int ua = oa.R * (kTK / 8), ub = ob.R * (kTK / 8), total = ua + ub;
+  for (int base = 0; base < total; base += kUnitsPerThread * static_cast<int>(blockDim.x)) {
+    double x[kUnitsPerThread][8];
+    int vv[kUnitsPerThread], kgs[kUnitsPerThread];
+    bool isA[kUnitsPerThread], live[kUnitsPerThread];
+#pragma unroll
+    for (int t = 0; t < kUnitsPerThread; ++t) {
+      const int u = base + t * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+      live[t] = u < total;
+      isA[t] = u < ua;
+      const OzOperand& o = isA[t] ? oa : ob;
+      int v = 0, kg = 0;
+      if (live[t]) oz_unit_coords(o, isA[t] ? u : u - ua, v, kg);
+      vv[t] = v;
+      kgs[t] = kg;
+      const int vg = o.v0 + v, k0 = kc * kTK + kg * 8;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        x[t][e] = (live[t] && vg < o.nvec && k < K) ? o.M[vg * o.sv + k * o.sk] : 0.0;
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kUnitsPerThread; ++t) {
+      if (!live[t]) continue;
+      const OzOperand& o = isA[t] ? oa : ob;
+      const int k0 = kc * kTK + kgs[t] * 8;
+      int kv[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int k = k0 + e;
+        kv[e] = (k < K) ? o.ksign * kev[k] : 0;
+        if (o.scaled && k < K) x[t][e] *= kss[k];
+      }
+      oz_split_unit(x[t], kv, o.ex[vv[t]] + 6, o.op, o.R, vv[t], kgs[t]);  // ex holds emax - 6
+    }
+  }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kFT, 1) k_oz_fused(OzFusedArgs a) {
+  using Tl = OzTile<BN>;
+  extern __shared__ __align__(1024) unsigned char oz_sm[];
+  __shared__ uint64_t full[kStages], mmad[kStages];
+  __shared__ uint32_t tmem_sh;
+  __shared__ int fail_sh;
+  __shared__ int exA_s[kTM], exB_s[BN];
+  __shared__ double ks_s[kMaxN];
+  __shared__ int kev_s[kMaxN];
+  __shared__ double colf[BN];
+  __shared__ int colx[BN];
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * BN;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int M = a.M, Nc = a.Nc, K = a.K;
+  const int nkc = (K + kTK - 1) / kTK;
+  const double* A = a.A + b * a.sA;
+  const double* B = a.B + b * a.sB;
+  const bool scA = a.ks_mode != 0 && a.ks != nullptr && !a.ks_on_b;
+  const bool scB = a.ks_mode != 0 && a.ks != nullptr && a.ks_on_b;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_sh)),
+                 "n"(Tl::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    for (int s2 = 0; s2 < kStages; ++s2) {
+      mbar_init(&full[s2], kFT);
+      mbar_init(&mmad[s2], 1);
+    }
+    fail_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  const double* ksb = a.ks ? a.ks + b * a.sks : nullptr;
+  for (int k = threadIdx.x; k < K; k += blockDim.x) {
+    ks_s[k] = oz_scale(ksb, a.ks_mode, k);
+    kev_s[k] = a.kexp ? a.kexp[b * static_cast<long long>(K) + k] : 0;
+  }
+  __syncthreads();
+  // exponents of the tile's rows of op(A) and columns of op(B)
+  auto vec_emax = [&](const double* Mp, long long sv, long long sk, int v, int nvec, int ksign,
+                      bool sc) -> int {
+    if (v >= nvec) return -100000;
+    return oz_vec_emax_lanes_k(Mp, sv, sk, v, K, ks_s, kev_s, ksign, sc, lane);
+  };
+  if (a.a_sk == 1) {
+    for (int v = warp; v < kTM; v += nw) {
+      const int e = vec_emax(A, a.a_sv, a.a_sk, i0 + v, M, 1, scA);
+      if (lane == 0) exA_s[v] = e - 6;
+    }
+  } else {
+    for (int v = threadIdx.x; v < kTM; v += blockDim.x) {
+      int emax = -100000;
+      if (i0 + v < M)
+        for (int k = 0; k < K; ++k) {
+          double x = A[(i0 + v) * a.a_sv + k * a.a_sk];
+          if (scA) x *= ks_s[k];
+          const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
+          if (E != 0) emax = max(emax, E - 1023 + kev_s[k]);
+        }
+      exA_s[v] = emax - 6;
+    }
+  }
+  if (a.b_sk == 1) {
+    for (int v = warp; v < BN; v += nw) {
+      const int e = vec_emax(B, a.b_sv, a.b_sk, j0 + v, Nc, -1, scB);
+      if (lane == 0) exB_s[v] = e - 6;
+    }
+  } else {
+    for (int v = threadIdx.x; v < BN; v += blockDim.x) {
+      int emax = -100000;
+      if (j0 + v < Nc)
+        for (int k = 0; k < K; ++k) {
+          double x = B[(j0 + v) * a.b_sv + k * a.b_sk];
+          if (scB) x *= ks_s[k];
+          const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
+          if (E != 0) emax = max(emax, E - 1023 - kev_s[k]);
+        }
+      exB_s[v] = emax - 6;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tbase = tmem_sh;
+  if (threadIdx.x < BN) {
+    const int q = threadIdx.x, j = j0 + q;
+    colf[q] = (j < Nc) ? oz_scale(a.cs ? a.cs + b * a.scs : nullptr, a.cs_mode, j) *
+                             ldexp(1.0, exB_s[q] - 21)
+                       : 0.0;
+    colx[q] = exB_s[q];
+  }
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((BN >> 3) << 17) | ((kTM >> 4) << 24);
+  int committed = -1;  // thread 0: last chunk whose MMAs were committed
+  for (int c = 0; c < nkc; ++c) {
+    const int st = c & 1;
+    unsigned char* smA = oz_sm + st * Tl::kStage;
+    unsigned char* smB = smA + kS * kATile;
+    if (c >= 2 && !mbar_wait(&mmad[st], ((c - 2) >> 1) & 1)) fail_sh = 1;
+    if (*reinterpret_cast<volatile int*>(&fail_sh)) break;
+    const OzOperand oa{A, a.a_sv, a.a_sk, i0, M, kTM, 1, scA, exA_s, smA};
+    const OzOperand ob{B, a.b_sv, a.b_sk, j0, Nc, BN, -1, scB, exB_s, smB};
+    oz_split_chunk2(oa, ob, K, c, ks_s, kev_s);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+    if (threadIdx.x == 0) {
+      if (!mbar_wait(&full[st], (c >> 1) & 1)) {
+        fail_sh = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int d = 0; d < kS; ++d)
+          for (int p = 0; p <= d; ++p) {
+            const int q = d - p;
+            for (int ks = 0; ks < kTK / 16; ++ks) {
+              const uint64_t ad = oz_desc(smem_u32(smA + p * kATile + ks * 256));
+              const uint64_t bd = oz_desc(smem_u32(smB + q * Tl::kBTile + ks * 256));
+              const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
+              asm volatile(
+                  "{\n .reg .pred pa;\n setp.ne.u32 pa, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tbase + d * BN),
+                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&mmad[st])));
+        committed = c;
+      }
+    }
+  }
+  // the MMAs of the last committed chunk (commit tracks all earlier MMAs too)
+  if (threadIdx.x == 0 && committed >= 0 &&
+      !mbar_wait(&mmad[committed & 1], (committed >> 1) & 1))
+    fail_sh = 1;
+  if (threadIdx.x == 0 && committed != nkc - 1) fail_sh = 1;
+  __syncthreads();
+  const bool ok = *reinterpret_cast<volatile int*>(&fail_sh) == 0;
+  if (!ok && threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // Recombination as in k_oz_mma: warps w and w + 4 share the TMEM lanes of
+    // quarter w % 4, each taking half of the columns; staged through shared
+    // memory for row-wise access to C.
+    const int quarter = warp & 3, half = warp >> 2;
+    const int rl = quarter * 32 + lane;
+    const int i = i0 + rl;
+    const bool row_ok = i < M;
+    const double rowf =
+        row_ok ? a.alpha * oz_scale(a.rs ? a.rs + b * a.srs : nullptr, a.rs_mode, i) *
+                     ldexp(1.0, exA_s[rl])
+               : 0.0;
+    const bool pow2 = (a.rs == nullptr || a.rs_mode == 0) && (a.cs == nullptr || a.cs_mode == 0) &&
+                      (a.alpha == 1.0 || a.alpha == -1.0);
+    const int rowx = exA_s[rl];
+    constexpr int kLd = BN + 1;
+    double* stg = reinterpret_cast<double*>(oz_sm);
+    for (int c = half * (BN / 32); c < (half + 1) * (BN / 32); ++c) {
+      uint32_t v[kS][16];
+#pragma unroll
+      for (int d = 0; d < kS; ++d) {
+        const uint32_t ta = tbase + (static_cast<uint32_t>(quarter * 32) << 16) + d * BN + c * 16;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
+              "=r"(v[d][6]), "=r"(v[d][7]), "=r"(v[d][8]), "=r"(v[d][9]), "=r"(v[d][10]), "=r"(v[d][11]),
+              "=r"(v[d][12]), "=r"(v[d][13]), "=r"(v[d][14]), "=r"(v[d][15])
+            : "r"(ta));
+      }
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (row_ok) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int jj = c * 16 + q;
+          long long hi = 0, lo = 0;
+#pragma unroll
+          for (int d = 0; d < 4; ++d)
+            hi += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (3 - d));
+#pragma unroll
+          for (int d = 4; d < kS; ++d)
+            lo += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (7 - d));
+          const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
+          double val;
+          bool ok2 = false;
+          if (pow2) val = scale_pow2(a.alpha < 0.0 ? -sum : sum, rowx + colx[jj] - 21, ok2);
+          if (!ok2) val = (sum * rowf) * colf[jj];
+          stg[rl * kLd + jj] = val;
+        }
+      }
+    }
+    __syncthreads();
+    double* C = a.C + b * a.sC;
+    for (int r = warp; r < kTM; r += nw) {
+      const int ii = i0 + r;
+      if (ii >= M) break;
+      for (int jj = lane; jj < BN; jj += 32) {
+        const int j = j0 + jj;
+        if (j < Nc) {
+          const size_t o = static_cast<size_t>(ii) * a.ldc + j;
+          double val = stg[r * kLd + jj];
+          if (a.beta != 0.0) val = fma(a.beta, C[o], val);
+          C[o] = val;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "n"(Tl::kTmemCols));
+}
+
+template <int BN>
+cudaError_t oz_run_fused(const OzProduct& g, int batch, void* scratch, int max_batch, int* status,
+                         cudaStream_t st) {
+  using Tl = OzTile<BN>;
+  const int M = g.M, Nc = g.Nc, K = g.K;
+  int* kexp = static_cast<int*>(scratch);  // [max_batch][K] balance exponents
+  const int nkc = (K + kTK - 1) / kTK;
+  const int smem = (nkc > 1 ? kStages : 1) * Tl::kStage;
+  cudaError_t e = cudaFuncSetAttribute(k_oz_fused<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStages * Tl::kStage);
+  if (e != cudaSuccess) return e;
+  for (int b0 = 0; b0 < batch; b0 += max_batch) {
+    const int nb = std::min(max_batch, batch - b0);
+    const double* ks = g.ks ? g.ks + b0 * g.sks : nullptr;
+    const int ks_mode = g.ks ? g.ks_mode : 0;
+    if (g.balance)
+      k_oz_kexp<<<dim3((K + 7) / 8, nb), 256, 0, st>>>(g.B + b0 * g.sB, g.sB, Nc, K, g.b_sv,
+                                                       g.b_sk, g.ks_on_b ? ks : nullptr, g.sks,
+                                                       g.ks_on_b ? ks_mode : 0, kexp);
+    OzFusedArgs f;
+    f.A = g.A + b0 * g.sA; f.sA = g.sA; f.a_sv = g.a_sv; f.a_sk = g.a_sk;
+    f.B = g.B + b0 * g.sB; f.sB = g.sB; f.b_sv = g.b_sv; f.b_sk = g.b_sk;
+    f.M = M; f.Nc = Nc; f.K = K;
+    f.ks = ks; f.sks = g.sks; f.ks_mode = ks_mode; f.ks_on_b = g.ks_on_b;
+    f.kexp = g.balance ? kexp : nullptr;
+    f.C = g.C + b0 * g.sC; f.sC = g.sC; f.ldc = g.ldc;
+    f.rs = g.rs ? g.rs + b0 * g.srs : nullptr; f.srs = g.srs; f.rs_mode = g.rs ? g.rs_mode : 0;
+    f.cs = g.cs ? g.cs + b0 * g.scs : nullptr; f.scs = g.scs; f.cs_mode = g.cs ? g.cs_mode : 0;
+    f.alpha = g.alpha; f.beta = g.beta;
+    f.status = status;
+    k_oz_fused<BN><<<dim3((Nc + BN - 1) / BN, (M + kTM - 1) / kTM, nb), kFT, smem, st>>>(f);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 size_t oz_slice_elems(int nvec, int K, int R) {
@@ -574,7 +964,14 @@ cudaError_t launch_ozaki_product(const OzProduct& g, int batch, void* scratch, i
                                  int* status, cudaStream_t st) {
   if (g.M <= 0 || g.Nc <= 0 || g.K <= 0 || batch <= 0) return cudaSuccess;
   if (g.K > kMaxN) return cudaErrorInvalidValue;  // the split kernel stages K scales in smem
-  if (g.Nc <= 32) return oz_run<32>(g, batch, scratch, max_batch, status, st);
+  // Products with a short inner dimension or few columns (the panel updates
+  // of the blocked QR) are cut into digits by the product kernel itself; the
+  // square products split both operands once in a separate kernel, which on
+  // this part measured faster than re-cutting op(A) for every column tile.
+  if (g.K <= 64 || g.Nc <= 32) {
+    if (g.Nc <= 32) return oz_run_fused<32>(g, batch, scratch, max_batch, status, st);
+    return oz_run_fused<64>(g, batch, scratch, max_batch, status, st);
+  }
   return oz_run<64>(g, batch, scratch, max_batch, status, st);
 }
 

@@ -302,13 +302,21 @@ __global__ void __launch_bounds__(kPT) k_qrb_panel(const double* Wsall, long lon
   auto vv = [&](int s, int r) -> double {
     return (r < s) ? 0.0 : (r == s ? 1.0 : P[static_cast<size_t>(s) * m + r]);
   };
-  for (int pr = wp; pr < w * w; pr += nw) {
-    const int s = pr / w, q = pr - s * w;
-    if (s >= q) continue;
-    double acc = 0.0;
-    for (int r = q + lane; r < m; r += 32) acc = fma(vv(s, r), vv(q, r), acc);
-    acc = qb_wsum(acc);
-    if (lane == 0) Gm[s][q] = acc;
+  // four pairs (s0 .. s0 + 3, q) per warp task, one butterfly for the four sums
+  const int groups = (w + 3) / 4;
+  for (int task = wp; task < w * groups; task += nw) {
+    const int q = task / groups, s0 = 4 * (task - q * groups);
+    if (s0 >= q) continue;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int r = q + lane; r < m; r += 32) {
+      const double vq = (r == q) ? 1.0 : P[static_cast<size_t>(q) * m + r];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (s0 + u < q) acc[u] = fma(P[static_cast<size_t>(s0 + u) * m + r], vq, acc[u]);
+    }
+    qb_wsum4(acc);
+    if (lane == 0)
+      for (int u = 0; u < 4 && s0 + u < q; ++u) Gm[s0 + u][q] = acc[u];
   }
   __syncthreads();
   if (wp == 0) {  // lanes over the rows i < q; four partial sums shorten the chain
@@ -409,10 +417,9 @@ int qr_blocked_launches(int n, int batch, int oz_batch) {
   const int panels = (n + kNB - 1) / kNB;
   const int chunks = (batch + oz_batch - 1) / oz_batch;
   // identity and finalize; one panel kernel per panel; two products (one
-  // split and one MMA kernel per chunk of the batch) per panel except the
-  // last, which has no trailing columns, and two per panel of the Q
-  // accumulation
-  return 2 + panels + (4 * panels - 2) * 2 * chunks;
+  // kernel per chunk of the batch) per panel except the last, which has no
+  // trailing columns, and two per panel of the Q accumulation
+  return 2 + panels + (4 * panels - 2) * chunks;
 }
 
 size_t qr_blocked_smem(int n) { return static_cast<size_t>(kNB) * n * sizeof(double); }
