@@ -345,6 +345,14 @@ cudaError_t stack_qr(dqmc_ctx* ctx, Group& g, double* Qt, double* Dv) {
 
 // ---- UDV stack steps ------------------------------------------------------
 
+// X = B ... B (U D) for a stack step: on the tensor cores where the
+// tensor-core products are in use (N >= 64), else on the FP64 pipe.
+cudaError_t stack_kron(dqmc_ctx* ctx, Group& g, const double* in, const KronArgs& a) {
+  if (ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz)
+    return launch_kron_tc(in, g.X, g.C, a, ctx->d_status, g.st);
+  return launch_kron_rows<double>(in, g.X, g.C, a, g.st);
+}
+
 // Right stack entry j from entry j-1 and slices cp[j-1]+1 .. cp[j].
 int stack_right(dqmc_ctx* ctx, Group& g, int j) {
   KronArgs a = kron_base(g, kB, kron_nv(g, true));
@@ -356,7 +364,7 @@ int stack_right(dqmc_ctx* ctx, Group& g, int j) {
   a.dir = 1;
   a.n_slices = g.cp[j] - g.cp[j - 1];
   DQ_CLASS(ctx, kTStackKron);
-  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.RU + (j - 1) * g.nn(), g.X, g.C, a, g.st));
+  DQ_LAUNCH(ctx, stack_kron(ctx, g, g.RU + (j - 1) * g.nn(), a));
   DQ_CLASS(ctx, kTQR);
   DQ_LAUNCH(ctx, stack_qr(ctx, g, g.RU + j * g.nn(), g.RD + j * g.N));
   GemmArgs m = gemm0(g.N);
@@ -380,7 +388,7 @@ int stack_left(dqmc_ctx* ctx, Group& g, int j) {
   a.dir = -1;
   a.n_slices = g.cp[j + 1] - g.cp[j];
   DQ_CLASS(ctx, kTStackKron);
-  DQ_LAUNCH(ctx, launch_kron_rows<double>(g.LU + (j + 1) * g.nn(), g.X, g.C, a, g.st));
+  DQ_LAUNCH(ctx, stack_kron(ctx, g, g.LU + (j + 1) * g.nn(), a));
   DQ_CLASS(ctx, kTQR);
   DQ_LAUNCH(ctx, stack_qr(ctx, g, g.LU + j * g.nn(), g.LD + j * g.N));
   GemmArgs m = gemm0(g.N);

@@ -87,6 +87,11 @@ cudaError_t launch_kron_cols(T* X, int batch, const KronArgs& a, cudaStream_t st
 template <typename T>
 cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* drift, int* status,
                                cudaStream_t st);
+// The FP64 Kronecker products of k_kron_rows<double> (same arguments, vectors
+// are rows) on the tcgen05 tensor cores, digit-sliced (k_kron_tc.cu); sides
+// Lx, Ly <= 16.
+cudaError_t launch_kron_tc(const double* in, double* out, int batch, const KronArgs& a, int* status,
+                           cudaStream_t st);
 cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
                                double* spin, cudaStream_t st);
 

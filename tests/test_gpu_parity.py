@@ -481,8 +481,9 @@ def test_drift_stays_small_with_eight_warps(prec):
 
 
 def test_tensor_core_fp64_products_match_fp64_pipe():
-    """Digit-sliced tcgen05 products (default for N >= 64) against the FP64
-    pipe on the same fields: G(0), G(tau) and the gradient agree to 1e-12."""
+    """The tensor-core path (digit-sliced tcgen05 products, blocked QR and
+    stack Kronecker products; default for N >= 64) against the FP64 pipe on
+    the same fields: G(0), G(tau) and the gradient agree to 1e-11."""
     g = _grp(16, 16, U=2.0, beta=10.0, dtau=0.125, ns=10, C=2)
     # N = 144 and 140: the last row tile (128 / 64 rows) and the last K chunk
     # (32) are partly padding
@@ -495,17 +496,19 @@ def test_tensor_core_fp64_products_match_fp64_pipe():
     gs = _grp(6, 6, U=2.0, beta=2.0, dtau=0.1, ns=5, C=1)  # N = 36: always the FP64 pipe
     groups = [g, g12, g14, gh, gs]
     # two FP64-accurate evaluations of G differ by rounding amplified by the
-    # conditioning of the chain: 1e-12 for the moderate groups, 1e-10 (the
-    # oracle tolerance) for the graded one; dropped small entries would show
-    # up at 1e-6 and above there
-    tol = [1e-12] * 4 + [1e-10] * 2 + [1e-12]
+    # conditioning of the chain.  The tensor-core path also pivots the stack
+    # QR panel-wise and forms the stack Kronecker products digit-sliced, so
+    # the moderate groups agree to 1e-11 (measured up to 1.2e-12), the graded
+    # one to 1e-10 (the oracle tolerance); dropped small entries would show up
+    # at 1e-6 and above there
+    tol = [1e-11] * 4 + [1e-10] * 2 + [1e-11]
     with _sim(groups, seed=5) as a, _sim(groups, seed=5) as b:
         b.set_gemm_mode("fp64")
         a.recompute_G()
         b.recompute_G()
         for c, t in enumerate(tol):
             assert _rel(a.G(c, 0), b.G(c, 0)) < t, c
-        gtol = [1e-12, 1e-12, 1e-12, 1e-10, 1e-12]  # per group
+        gtol = [1e-11, 1e-11, 1e-11, 1e-10, 1e-11]  # per group
         for x, y, t in zip(a.gtau(), b.gtau(), gtol):
             np.testing.assert_allclose(x, y, rtol=0, atol=t * np.max(np.abs(y)))
         for x, y in zip(a.grad(), b.grad()):
