@@ -63,16 +63,6 @@ __device__ __forceinline__ bool tc_wait(uint64_t* bar, int parity) {
   return done != 0;
 }
 
-// Unbiased exponent of the largest element of x[0 .. n); -100000 if all zero.
-__device__ __forceinline__ int tc_emax(const double* x, int n) {
-  int emax = -100000;
-  for (int k = 0; k < n; ++k) {
-    const int E = static_cast<int>((__double_as_longlong(x[k]) >> 52) & 0x7FF);
-    if (E != 0) emax = max(emax, E - 1023);
-  }
-  return emax;
-}
-
 // The 8 digits of x aligned to emax (as k_ozaki.cu), BF16 bit patterns.
 __device__ __forceinline__ void tc_digits(double x, int emax, uint16_t (&dg)[kS]) {
   const long long bits = __double_as_longlong(x);
@@ -246,47 +236,50 @@ __global__ void __launch_bounds__(kTC) k_kron_tc(const double* in, double* out, 
       ok = __syncthreads_and(fail_sh == 0) != 0;
       asm volatile("tcgen05.fence::after_thread_sync;");
       if (!ok) break;
-      uint32_t acc[kS][16];
-#pragma unroll
-      for (int d = 0; d < kS; ++d) {
-        const uint32_t ta = tbase + (static_cast<uint32_t>(warp * 32) << 16) + d * kK;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(acc[d][0]), "=r"(acc[d][1]), "=r"(acc[d][2]), "=r"(acc[d][3]), "=r"(acc[d][4]),
-              "=r"(acc[d][5]), "=r"(acc[d][6]), "=r"(acc[d][7]), "=r"(acc[d][8]), "=r"(acc[d][9]),
-              "=r"(acc[d][10]), "=r"(acc[d][11]), "=r"(acc[d][12]), "=r"(acc[d][13]),
-              "=r"(acc[d][14]), "=r"(acc[d][15])
-            : "r"(ta));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
       // recombination: (hi + 2^-28 lo) 2^{e_r + f_j - 21}, the power of two in
-      // the exponent field (FP64 products where it would leave the normal range)
+      // the exponent field (FP64 products where it would leave the normal
+      // range); the accumulators are read eight columns at a time
       const int* exj = dir == 0 ? exx : exy;
-      if (live) {
 #pragma unroll
-        for (int j = 0; j < kK; ++j) {
-          if (j >= klen) continue;
-          long long hi = 0, lo = 0;
+      for (int half = 0; half < 2; ++half) {
+        uint32_t acc[kS][8];
 #pragma unroll
-          for (int d = 0; d < 4; ++d)
-            hi += static_cast<long long>(__float2int_rn(__uint_as_float(acc[d][j]))) << (7 * (3 - d));
+        for (int d = 0; d < kS; ++d) {
+          const uint32_t ta = tbase + (static_cast<uint32_t>(warp * 32) << 16) + d * kK + half * 8;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+              : "=r"(acc[d][0]), "=r"(acc[d][1]), "=r"(acc[d][2]), "=r"(acc[d][3]), "=r"(acc[d][4]),
+                "=r"(acc[d][5]), "=r"(acc[d][6]), "=r"(acc[d][7])
+              : "r"(ta));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (live) {
 #pragma unroll
-          for (int d = 4; d < kS; ++d)
-            lo += static_cast<long long>(__float2int_rn(__uint_as_float(acc[d][j]))) << (7 * (7 - d));
-          const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
-          const int e2 = (emax - 6) + exj[j] - 21;
-          const long long bits = __double_as_longlong(sum);
-          const int E = static_cast<int>((bits >> 52) & 0x7FF), E2 = E + e2;
-          double val;
-          if (E != 0 && E != 0x7FF && E2 > 0 && E2 < 2047)
-            val = __longlong_as_double((bits & ~(0x7FFLL << 52)) | (static_cast<long long>(E2) << 52));
-          else
-            val = sum * ldexp(1.0, emax - 6) * ldexp(1.0, exj[j] - 21);
-          // rows are read above and written only here, each by its owner
-          if (dir == 0)
-            V[vi * N + j + Lx * o] = val;
-          else
-            V[vi * N + o + Lx * j] = val;
+          for (int jq = 0; jq < 8; ++jq) {
+            const int j = half * 8 + jq;
+            if (j >= klen) continue;
+            long long hi = 0, lo = 0;
+#pragma unroll
+            for (int d = 0; d < 4; ++d)
+              hi += static_cast<long long>(__float2int_rn(__uint_as_float(acc[d][jq]))) << (7 * (3 - d));
+#pragma unroll
+            for (int d = 4; d < kS; ++d)
+              lo += static_cast<long long>(__float2int_rn(__uint_as_float(acc[d][jq]))) << (7 * (7 - d));
+            const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
+            const int e2 = (emax - 6) + exj[j] - 21;
+            const long long bits = __double_as_longlong(sum);
+            const int E = static_cast<int>((bits >> 52) & 0x7FF), E2 = E + e2;
+            double val;
+            if (E != 0 && E != 0x7FF && E2 > 0 && E2 < 2047)
+              val = __longlong_as_double((bits & ~(0x7FFLL << 52)) | (static_cast<long long>(E2) << 52));
+            else
+              val = sum * ldexp(1.0, emax - 6) * ldexp(1.0, exj[j] - 21);
+            // rows are read above and written only here, each by its owner
+            if (dir == 0)
+              V[vi * N + j + Lx * o] = val;
+            else
+              V[vi * N + o + Lx * j] = val;
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
