@@ -1134,12 +1134,18 @@ int measure_gtau_group(dqmc_ctx* ctx, Group& g, double* dst) {
     ga.cp = g.d_cp_gtau;
     ga.mat_stride = g.nn();
     ga.bins = g.bins;
+    // FP64 groups on the tensor cores where the tensor-core products are in
+    // use (measured faster than the FP64 pipe); float-pair groups keep their
+    // float-pair propagation, which measured faster than the tensor path
+    const bool tc = ctx->gemm_mode == DQMC_GEMM_TENSOR && g.oz && !pair;
     ga.kind = kB; ga.vec_is_col = 1; ga.bin_slot = 0;
     DQ_CLASS(ctx, kTGtauProp);
-    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A1, batch, ga, pair, g.st));
+    DQ_LAUNCH(ctx, tc ? launch_gtau_tc(g.A1, batch, ga, ctx->d_status, g.st)
+                      : launch_gtau_propagate(g.A1, batch, ga, pair, g.st));
     ga.kind = kBIT; ga.vec_is_col = 0; ga.bin_slot = 1;
     DQ_CLASS(ctx, kTGtauProp);
-    DQ_LAUNCH(ctx, launch_gtau_propagate(g.A2, batch, ga, pair, g.st));
+    DQ_LAUNCH(ctx, tc ? launch_gtau_tc(g.A2, batch, ga, ctx->d_status, g.st)
+                      : launch_gtau_propagate(g.A2, batch, ga, pair, g.st));
     DQ_CLASS(ctx, kTGtauFinal);
     DQ_LAUNCH(ctx, launch_gtau_finalize(g.bins, dst, g.C, g.L, g.p.Lx, g.p.Ly, g.st));
   }

@@ -182,6 +182,10 @@ struct GtauArgs {
 // pair: propagate in float pairs (groups whose working precision is df32).
 cudaError_t launch_gtau_propagate(double* X, int batch, const GtauArgs& a, bool pair,
                                   cudaStream_t st);
+// The same propagation and binning with the Kronecker products on the tcgen05
+// tensor cores (k_kron_tc.cu), FP64-accurate; sides Lx, Ly <= 16.
+cudaError_t launch_gtau_tc(const double* X, int batch, const GtauArgs& a, int* status,
+                           cudaStream_t st);
 // out[chain][l][k] from the bins (spin average, momentum transform).
 cudaError_t launch_gtau_finalize(const double* bins, double* out, int C, int L, int Lx, int Ly,
                                  cudaStream_t st);
