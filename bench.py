@@ -224,32 +224,42 @@ def measured_peaks():
 FP64_PEAK = 152 * 2 * 2 * 2.07e9 / 1e12
 DF32_PEAK = 2 * 152 * 128 * 2.07e9 / 14 / 1e12
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of a kernel on the 64-chain 16x16 case, whose launches do the same
-# work as the benchmark's (one slice of 64 chains; 64 QRs of order 256), keyed
-# by (class, precision).  Each entry names the source file of the kernel and
-# the SHA-256 prefix that file had when the counters were taken: if the file
-# has changed since, the entry is stale and the roofline line reports null.
-TRAFFIC = {}
+# DRAM bytes per class launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# summed over the kernels of one launch of the class) from one ncu capture on
+# the 64-chain 16x16 case (`bench.py --profile-case`), whose launches do the
+# same work as the benchmark's (one slice of 64 chains; 64 QRs of order 256;
+# one stack step of 64 chains), keyed by (class, precision).  Each entry names
+# the source files of its kernels and the SHA-256 prefix they had when the
+# counters were taken: if a file has changed since, the entry is stale and the
+# roofline line reports null.  (profiles/launches_profile_case_16x16.md)
+TRAFFIC = {
+    # panel x 8, fused rank-32 products x 30, finalize: one blocked QR launch
+    ("qr_pivot", None): (688e6, ("k_qr_blocked.cu", "k_ozaki.cu"), "017c3f417ec0f1fb"),
+    ("metropolis", "df32"): (33.69e6, ("k_sweep.cu",), "7cbb24368c12820d"),
+    ("stack_kron", None): (34.13e6, ("k_kron_tc.cu",), "5046ac778a31eae9"),
+}
 
 
-def _source_sha16(rel):
+def _source_sha16(files):
     import hashlib
+    h = hashlib.sha256()
     try:
-        with open(os.path.join(ROOT, "paper_1504_05090_gb300", "csrc", rel), "rb") as fh:
-            return hashlib.sha256(fh.read()).hexdigest()[:16]
+        for rel in files:
+            with open(os.path.join(ROOT, "paper_1504_05090_gb300", "csrc", rel), "rb") as fh:
+                h.update(fh.read())
     except OSError:
         return None
+    return h.hexdigest()[:16]
 
 
 def traffic_bytes(cls, precision):
-    """Measured DRAM bytes per launch of the class's dominant kernel, or None
-    when there is no capture of the current source."""
+    """Measured DRAM bytes per launch of the class, or None when there is no
+    capture of the current source."""
     ent = TRAFFIC.get((cls, precision), TRAFFIC.get((cls, None)))
     if ent is None:
         return None
-    nbytes, src, sha = ent
-    return nbytes if _source_sha16(src) == sha else None
+    nbytes, files, sha = ent
+    return int(nbytes) if _source_sha16(files) == sha else None
 
 
 def class_work(cls, acceptance, precision):
@@ -266,7 +276,10 @@ def class_work(cls, acceptance, precision):
         # cores each FP64 product is 36 BF16 digit products.
         fp64eq = C * g3 * (2 * nc + 4 * nc + 6 * (nc + 1))
         return "tensor", 36 * fp64eq
-    if cls == "qr_pivot":  # Householder R and explicit Q, both stacks
+    if cls == "qr_pivot":
+        # Householder R and explicit Q, both stacks, counted as FP64 flops:
+        # the panels run on the FP64 pipe, the trailing updates and the
+        # accumulation of Q (about 90 % of the flops) on the tensor cores
         return "alu64", C * 2 * nc * (8.0 / 3.0) * N ** 3
     if cls == "gj_inverse":  # nc recomputes + (nc + 1) stabilisation points for G(tau)
         # (float-pair groups invert the G(tau) points in float pairs, the class below)
@@ -275,10 +288,14 @@ def class_work(cls, acceptance, precision):
         return "alu32x2", C * (nc + 1) * g3
     if cls in ("stack_kron", "gtau_propagate"):
         # two matrices (right and left stack; G(l,0) and Y) x L slices x N vectors
-        # x 2N(Lx+Ly) flops per Kronecker application; G(tau) is propagated in
-        # the working precision of float-pair groups
-        pair = cls == "gtau_propagate" and precision == "df32"
-        return ("alu32x2" if pair else "alu64"), C * 2 * L * N * 2 * N * (Lx + Ly)
+        # x 2N(Lx+Ly) flops per Kronecker application.  The stack products (and
+        # the G(tau) propagation of FP64 groups) run on the tensor cores as 36
+        # BF16 digit products per FP64 product; float-pair groups propagate
+        # G(tau) in float pairs on the FP32 pipe
+        fp64eq = C * 2 * L * N * 2 * N * (Lx + Ly)
+        if cls == "gtau_propagate" and precision == "df32":
+            return "alu32x2", fp64eq
+        return "tensor", 36 * fp64eq
     if cls == "metropolis":  # rank-1 Sherman-Morrison update per accepted flip
         return ("alu32x2" if precision == "df32" else "alu"), acceptance * C * N * L * 2.0 * N * N
     if cls == "wrap":  # B G B^-1 by Kronecker factors: 2 sides x N vectors x 2N(Lx+Ly)
