@@ -35,6 +35,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "oz_compose.cuh"
 
 namespace dqmc {
 namespace {
@@ -265,16 +266,6 @@ __device__ __forceinline__ void oz_issue_chunk(unsigned char* stage, const __nv_
   }
 }
 
-// d 2^e for a normal double d by adding e to its exponent field (integer
-// arithmetic); ok = false for zero, subnormal or overflowing results.
-__device__ __forceinline__ double scale_pow2(double d, int e, bool& ok) {
-  const long long bits = __double_as_longlong(d);
-  const int E = static_cast<int>((bits >> 52) & 0x7FF);
-  const int E2 = E + e;
-  ok = E != 0 && E != 0x7FF && E2 > 0 && E2 < 2047;
-  return __longlong_as_double((bits & ~(0x7FFLL << 52)) | (static_cast<long long>(E2 & 0x7FF) << 52));
-}
-
 // C (M x Nc, leading dimension ldc) = alpha diag(rs) [digit product] diag(cs)
 // + beta C for each batch entry; K is the inner dimension.
 struct OzMmaArgs {
@@ -299,13 +290,22 @@ struct OzMmaArgs {
   int* status;
 };
 
+// 256 threads.  Thread 0 issues the MMAs of each K chunk once its copies
+// have landed; thread 32 (warp 1) is the producer: it loads chunk c into stage
+// c & 1 as soon as the MMAs of chunk c - 2 that read that stage are done, so
+// the copy of chunk c + 1 runs while the tensor pipe works on chunk c (the
+// issuing thread blocks while the MMA queue is full and cannot do both).  All
+// eight warps then drain TMEM: warp w reads the lanes (rows) 32 (w & 3) ..
+// and half w >> 2 of the columns.
 template <int BN>
-__global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
+__global__ void __launch_bounds__(256) k_oz_mma(OzMmaArgs a) {
   using Tl = OzTile<BN>;
   extern __shared__ __align__(1024) unsigned char oz_sm[];
   __shared__ uint64_t full[kStages], mmad[kStages];
   __shared__ uint32_t tmem_sh;
   __shared__ int fail_sh;
+  __shared__ int loaded[kStages], consumed[kStages];  // last chunk loaded into / read from a stage
+  __shared__ int committed_sh;
   __shared__ double colf[BN];  // cs_j 2^{f_j - 21} of this CTA's columns
   __shared__ int colx[BN];     // f_j of this CTA's columns
   const int b = blockIdx.z;
@@ -315,8 +315,8 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   const int nrtA = (M + kTM - 1) / kTM, nrtB = (Nc + BN - 1) / BN, nkc = (a.K + kTK - 1) / kTK;
   const __nv_bfloat16* As = a.As + b * a.sAs;
   const __nv_bfloat16* Bs = a.Bs + b * a.sBs;
-  if (threadIdx.x >= 128 - BN) {
-    const int q = threadIdx.x - (128 - BN), j = j0 + q;
+  if (threadIdx.x >= 256 - BN) {
+    const int q = threadIdx.x - (256 - BN), j = j0 + q;
     colf[q] = (j < Nc) ? oz_scale(a.cs ? a.cs + b * a.scs : nullptr, a.cs_mode, j) *
                              ldexp(1.0, a.exB[b * a.sExB + j] - 21)
                        : 0.0;
@@ -332,8 +332,10 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
     for (int s2 = 0; s2 < kStages; ++s2) {
       mbar_init(&full[s2], 1);
       mbar_init(&mmad[s2], 1);
+      loaded[s2] = consumed[s2] = -1;
     }
     fail_sh = 0;
+    committed_sh = -1;
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -342,22 +344,27 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
   const uint32_t tbase = tmem_sh;
   // kind::f16 instruction descriptor: D = F32, A = B = BF16, both K-major, N, M.
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((BN >> 3) << 17) | ((kTM >> 4) << 24);
-  if (threadIdx.x == 0) {
-    // Producer and MMA issuer.  Chunk c sits in stage c & 1.  After the MMAs
-    // of chunk c are queued, the MMAs of chunk c - 1 (queued earlier, so done
-    // first) are awaited and chunk c + 1 is loaded into their stage while the
-    // tensor pipe works on chunk c.
-    int pend_load[kStages] = {-1, -1};  // parity of an outstanding load per stage
-    int committed = -1;                 // last chunk whose MMAs were committed
-    oz_issue_chunk<BN>(oz_sm, As, Bs, blockIdx.y, blockIdx.x, 0, nrtA, nrtB, nkc, &full[0]);
-    pend_load[0] = 0;
+  volatile int* fail_v = &fail_sh;
+  if (threadIdx.x == 32) {  // producer
+    for (int c = 0; c < nkc && !*fail_v; ++c) {
+      const int st = c & 1;
+      // stage st was last read by the MMAs of chunk c - 2
+      if (c >= kStages && !mbar_wait(&mmad[st], ((c - kStages) >> 1) & 1)) {
+        *fail_v = 1;
+        break;
+      }
+      oz_issue_chunk<BN>(oz_sm + st * Tl::kStage, As, Bs, blockIdx.y, blockIdx.x, c, nrtA, nrtB,
+                         nkc, &full[st]);
+      loaded[st] = c;
+    }
+  } else if (threadIdx.x == 0) {  // MMA issuer
     for (int c = 0; c < nkc; ++c) {
       const int st = c & 1;
       if (!mbar_wait(&full[st], (c >> 1) & 1)) {
-        fail_sh = 1;
+        *fail_v = 1;
         break;
       }
-      pend_load[st] = -1;
+      consumed[st] = c;
       asm volatile("tcgen05.fence::after_thread_sync;");
       unsigned char* smA = oz_sm + st * Tl::kStage;
       unsigned char* smB = smA + kS * kATile;
@@ -376,25 +383,19 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
         }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mmad[st])));
-      committed = c;
-      if (c + 1 < nkc) {
-        const int so = st ^ 1;
-        if (c >= 1 && !mbar_wait(&mmad[so], ((c - 1) >> 1) & 1)) {
-          fail_sh = 1;
-          break;
-        }
-        oz_issue_chunk<BN>(oz_sm + so * Tl::kStage, As, Bs, blockIdx.y, blockIdx.x, c + 1, nrtA,
-                           nrtB, nkc, &full[so]);
-        pend_load[so] = ((c + 1) >> 1) & 1;
-      }
-    }
-    if (fail_sh) {  // drain what is still in flight before TMEM and smem go away
-      for (int s2 = 0; s2 < kStages; ++s2)
-        if (pend_load[s2] >= 0) mbar_wait(&full[s2], pend_load[s2]);
-      if (committed >= 0) mbar_wait(&mmad[committed & 1], (committed >> 1) & 1);
+      committed_sh = c;
+      if (*fail_v) break;
     }
   }
   __syncthreads();
+  if (fail_sh && threadIdx.x == 0) {
+    // drain what is still in flight before TMEM and smem go away: loads that
+    // no MMA waited for, and the last committed MMAs (which cover all earlier)
+    for (int s2 = 0; s2 < kStages; ++s2)
+      if (loaded[s2] > consumed[s2]) mbar_wait(&full[s2], (loaded[s2] >> 1) & 1);
+    const int cm = committed_sh;
+    if (cm >= 0) mbar_wait(&mmad[cm & 1], (cm >> 1) & 1);
+  }
   // Everyone waits for the MMAs of the last chunk (tcgen05.commit tracks all
   // earlier MMAs of the issuing thread, so this covers every chunk).
   bool ok = fail_sh == 0;
@@ -409,12 +410,12 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
     // Recombination.  Every accumulator holds an integer P_d (a sum of digit
     // products); sum_d P_d 2^{-7d} = 2^{-21} (hi + 2^{-28} lo) with the exact
     // 64-bit integers hi = sum_{d<4} P_d 2^{7(3-d)} and lo = sum_{d>=4} P_d
-    // 2^{7(7-d)} (both below 2^47, so exact in FP64): two conversions and one
-    // FMA round the sum once.  Without row and column scales (alpha = +-1)
-    // the power of two 2^{e_i + f_j - 21} and the sign go into the exponent
-    // and sign fields as integers; otherwise the scales are two FP64
-    // products.
-    const int i = i0 + warp * 32 + lane;
+    // 2^{7(7-d)} (both below 2^47), rounded once to FP64 by oz_compose with
+    // integer instructions.  Without row and column scales (alpha = +-1) the
+    // power of two 2^{e_i + f_j - 21} and the sign go into the exponent and
+    // sign fields there; otherwise the scales are two FP64 products.
+    const int quarter = warp & 3, half = warp >> 2;
+    const int i = i0 + quarter * 32 + lane;
     const bool row_ok = i < M;
     const double rowf =
         row_ok ? a.alpha * oz_scale(a.rs ? a.rs + b * a.srs : nullptr, a.rs_mode, i) *
@@ -424,11 +425,11 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
                       (a.alpha == 1.0 || a.alpha == -1.0);
     const int rowx = row_ok ? a.exA[b * a.sExA + i] : 0;
     double* C = a.C + b * a.sC;
-    for (int c = 0; c < BN / 16; ++c) {
+    for (int c = half * (BN / 32); c < (half + 1) * (BN / 32); ++c) {
       uint32_t v[kS][16];
 #pragma unroll
       for (int d = 0; d < kS; ++d) {
-        const uint32_t ta = tbase + (static_cast<uint32_t>(warp * 32) << 16) + d * BN + c * 16;
+        const uint32_t ta = tbase + (static_cast<uint32_t>(quarter * 32) << 16) + d * BN + c * 16;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
@@ -449,11 +450,10 @@ __global__ void __launch_bounds__(128) k_oz_mma(OzMmaArgs a) {
 #pragma unroll
             for (int d = 4; d < kS; ++d)
               lo += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (7 - d));
-            const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
             double val;
             bool ok2 = false;
-            if (pow2) val = scale_pow2(a.alpha < 0.0 ? -sum : sum, rowx + colx[jj] - 21, ok2);
-            if (!ok2) val = (sum * rowf) * colf[jj];
+            if (pow2) val = oz_compose(hi, lo, rowx + colx[jj] - 21, a.alpha < 0.0, ok2);
+            if (!ok2) val = (oz_compose(hi, lo, 0, false, ok2) * rowf) * colf[jj];
             const size_t o = static_cast<size_t>(i) * a.ldc + j;
             if (a.beta != 0.0) val = fma(a.beta, C[o], val);
             C[o] = val;
@@ -826,11 +826,10 @@ __global__ void __launch_bounds__(kFT, 1) k_oz_fused(OzFusedArgs a) {
 #pragma unroll
           for (int d = 4; d < kS; ++d)
             lo += static_cast<long long>(__float2int_rn(__uint_as_float(v[d][q]))) << (7 * (7 - d));
-          const double sum = fma(static_cast<double>(lo), 0x1p-28, static_cast<double>(hi));
           double val;
           bool ok2 = false;
-          if (pow2) val = scale_pow2(a.alpha < 0.0 ? -sum : sum, rowx + colx[jj] - 21, ok2);
-          if (!ok2) val = (sum * rowf) * colf[jj];
+          if (pow2) val = oz_compose(hi, lo, rowx + colx[jj] - 21, a.alpha < 0.0, ok2);
+          if (!ok2) val = (oz_compose(hi, lo, 0, false, ok2) * rowf) * colf[jj];
           stg[rl * kLd + jj] = val;
         }
       }
@@ -945,7 +944,7 @@ cudaError_t oz_run(const OzProduct& g, int batch, void* scratch, int max_batch, 
     m.cs = g.cs ? g.cs + b0 * g.scs : nullptr; m.scs = g.scs; m.cs_mode = g.cs ? g.cs_mode : 0;
     m.alpha = g.alpha; m.beta = g.beta;
     m.status = status;
-    k_oz_mma<BN><<<dim3((Nc + BN - 1) / BN, (M + kTM - 1) / kTM, nb), 128, smem, st>>>(m);
+    k_oz_mma<BN><<<dim3((Nc + BN - 1) / BN, (M + kTM - 1) / kTM, nb), 256, smem, st>>>(m);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
