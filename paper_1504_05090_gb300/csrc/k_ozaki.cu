@@ -125,12 +125,24 @@ struct OzSplitOp {
 };
 
 // Both operands of a product in one launch: blocks [0, opA.blocks) split the
-// rows of op(A), the others the columns of op(B).  One warp per vector: the
-// element (times the inner scale, times 2^{ksign kexp[k]} when balancing; the
-// power of two only moves the digit alignment, as an integer exponent
-// offset) is cut into 8 digit slices written in the tile-blocked layout
-// (rows padded to a multiple of R, K to a multiple of the chunk, zero
-// padding), with the scale exponent ex[v].
+// rows of op(A), the others the columns of op(B).  A block takes kSV vectors:
+// it stages them (times the inner scale) in shared memory with coalesced
+// loads whichever way the vectors lie in memory, finds each vector's largest
+// exponent (plus 2^{ksign kexp[k]} when balancing; the power of two only
+// moves the digit alignment, as an integer exponent offset), and cuts every
+// element into 8 digit slices written in the tile-blocked layout (rows padded
+// to a multiple of R, K to a multiple of the chunk, zero padding), with the
+// scale exponent ex[v].
+constexpr int kSV = 32;  // vectors per split block
+__host__ __device__ constexpr int oz_split_ld(int n) { return ((n + 7) & ~7) + 1; }
+__host__ __device__ constexpr size_t oz_split_smem(int n) {
+  return static_cast<size_t>(kSV) * oz_split_ld(n) * sizeof(double);
+}
+// Position of element k within a staged vector: each group of 8 is rotated by
+// (k / 16) mod 8, so that the 16 lanes of a half warp reading element e of
+// their groups 8L + e hit 16 different bank pairs.
+__device__ __forceinline__ int oz_swz(int k) { return (k & ~7) | ((k + (k >> 4)) & 7); }
+
 __global__ void __launch_bounds__(256) k_oz_split(OzSplitOp opA, OzSplitOp opB, int n,
                                                  const int* kexpall) {
   const bool isA = static_cast<int>(blockIdx.x) < opA.blocks;
@@ -140,9 +152,10 @@ __global__ void __launch_bounds__(256) k_oz_split(OzSplitOp opA, OzSplitOp opB, 
   const int nvec = o.nvec, R = o.R;
   const long long sv = o.sv, sk = o.sk;
   const int ks_mode = o.ks_mode;
-  const int nrt = (nvec + R - 1) / R, nkc = (n + kTK - 1) / kTK, np = nkc * kTK;
+  const int nrt = (nvec + R - 1) / R, nkc = (n + kTK - 1) / kTK;
   const int b = blockIdx.y;
   const double* M = o.M + b * o.sM;
+  extern __shared__ __align__(16) double xs[];  // [kSV][oz_split_ld(n)], swizzled along k
   __shared__ double ksv[kMaxN];
   __shared__ int kev[kMaxN];
   const double* ks = o.ks ? o.ks + b * o.sks : nullptr;
@@ -151,26 +164,72 @@ __global__ void __launch_bounds__(256) k_oz_split(OzSplitOp opA, OzSplitOp opB, 
     kev[k] = kexpall ? o.ksign * kexpall[b * static_cast<long long>(n) + k] : 0;
   }
   __syncthreads();
-  const int v = bx * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (v >= nrt * R) return;
+  const int v0 = bx * kSV, ld = oz_split_ld(n);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (v0 >= nrt * R) return;
+  // 1. stage the block's vectors; lanes run along the contiguous index, and
+  // every thread has 8 loads in flight before it stores
+  constexpr int kU = 8;
+  if (sv == 1) {
+    const int v = v0 + lane;
+    for (int k0 = warp; k0 < n; k0 += nw * kU) {
+      double x[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int k = k0 + u * nw;
+        x[u] = (v < nvec && k < n) ? M[v + k * sk] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int k = k0 + u * nw;
+        if (k < n) xs[lane * ld + oz_swz(k)] = (ks_mode != 0) ? x[u] * ksv[k] : x[u];
+      }
+    }
+  } else {
+    for (int r = warp; r < kSV; r += nw) {
+      const int v = v0 + r;
+      for (int k0 = lane; k0 < n; k0 += 32 * kU) {
+        double x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int k = k0 + 32 * u;
+          x[u] = (v < nvec && k < n) ? M[v * sv + k * sk] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int k = k0 + 32 * u;
+          if (k < n) xs[r * ld + oz_swz(k)] = (ks_mode != 0) ? x[u] * ksv[k] : x[u];
+        }
+      }
+    }
+  }
+  __syncthreads();
   __nv_bfloat16* out = o.out + b * o.sOut;
-  // Each lane owns 8 consecutive K elements: they are adjacent in the core-matrix
-  // layout (np is a multiple of 32), so each digit slice takes one 16-byte store.
-  if (v >= nvec) {  // padding rows of the last row tile
-    for (int k0 = lane * 8; k0 < np; k0 += 256)
-      for (int p = 0; p < kS; ++p)
-        *reinterpret_cast<uint4*>(out + oz_offset(p, v, k0, R, nrt, nkc)) = make_uint4(0, 0, 0, 0);
-    return;
+  // 2. exponent of every vector, one warp per vector
+  __shared__ int exs[kSV];
+  for (int r = warp; r < kSV; r += nw) {
+    const double* xr = xs + r * ld;
+    int emax = -100000;
+    for (int k = lane; k < n; k += 32) {
+      const int E = static_cast<int>((__double_as_longlong(xr[oz_swz(k)]) >> 52) & 0x7FF);
+      if (E != 0) emax = max(emax, E - 1023 + kev[k]);
+    }
+    for (int q = 16; q > 0; q >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, q));
+    if (lane == 0) {
+      exs[r] = emax;
+      if (v0 + r < nvec) o.ex[b * o.sEx + v0 + r] = emax - 6;
+    }
   }
-  int emax = -100000;
-  for (int k = lane; k < n; k += 32) {
-    const double x = (ks_mode != 0) ? M[v * sv + k * sk] * ksv[k] : M[v * sv + k * sk];
-    const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
-    if (E != 0) emax = max(emax, E - 1023 + kev[k]);
-  }
-  for (int q = 16; q > 0; q >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, q));
-  if (lane == 0) o.ex[b * o.sEx + v] = emax - 6;
-  for (int k0 = lane * 8; k0 < np; k0 += 256) {
+  __syncthreads();
+  // 3. digits: a warp task is 8 vectors x one K chunk of 32, lane = (vector
+  // r & 7, 8-element group of the chunk), so that the 32 16-byte stores of a
+  // slice fill one contiguous 512-byte run of the core-matrix layout
+  const int ntask = (kSV / 8) * nkc;
+  for (int task = warp; task < ntask; task += nw) {
+    const int rg = task / nkc, kc = task - rg * nkc;
+    const int r = rg * 8 + (lane & 7), v = v0 + r, k0 = kc * kTK + (lane >> 3) * 8;
+    const double* xr = xs + r * ld;
+    const int emax = exs[r];
     unsigned long long al[8];
     float sg[8];
 #pragma unroll
@@ -178,9 +237,8 @@ __global__ void __launch_bounds__(256) k_oz_split(OzSplitOp opA, OzSplitOp opB, 
       const int k = k0 + e;
       al[e] = 0;
       sg[e] = 1.0f;
-      if (k < n) {
-        const double x = (ks_mode != 0) ? M[v * sv + k * sk] * ksv[k] : M[v * sv + k * sk];
-        const long long bits = __double_as_longlong(x);
+      if (k < n && v < nvec) {  // padding rows and columns give zero digits
+        const long long bits = __double_as_longlong(xr[oz_swz(k)]);
         const int E = static_cast<int>((bits >> 52) & 0x7FF);
         if (E != 0) {  // zero and subnormal inputs contribute zero digits
           const unsigned long long mant =
@@ -917,6 +975,9 @@ cudaError_t oz_run(const OzProduct& g, int batch, void* scratch, int max_batch, 
   cudaError_t e = cudaFuncSetAttribute(k_oz_mma<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        kStages * Tl::kStage);
   if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_oz_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(oz_split_smem(kMaxN)));
+  if (e != cudaSuccess) return e;
   const int rowsA = (M + kTM - 1) / kTM * kTM, rowsB = (Nc + BN - 1) / BN * BN;
   for (int b0 = 0; b0 < batch; b0 += max_batch) {
     const int nb = std::min(max_batch, batch - b0);
@@ -931,10 +992,10 @@ cudaError_t oz_run(const OzProduct& g, int batch, void* scratch, int max_batch, 
     const int* kx = g.balance ? kexp : nullptr;
     // rows of op(A) [diag(ks)] and columns of [diag(ks)] op(B), one launch
     OzSplitOp oa{g.A + b0 * g.sA, g.sA, M, kTM, g.a_sv, g.a_sk, on_b ? nullptr : ks, g.sks,
-                 on_b ? 0 : ks_mode, 1, As, slA, exA, M, (rowsA + 7) / 8};
+                 on_b ? 0 : ks_mode, 1, As, slA, exA, M, (rowsA + kSV - 1) / kSV};
     OzSplitOp ob{g.B + b0 * g.sB, g.sB, Nc, BN, g.b_sv, g.b_sk, on_b ? ks : nullptr, g.sks,
-                 on_b ? ks_mode : 0, -1, Bs, slB, exB, Nc, (rowsB + 7) / 8};
-    k_oz_split<<<dim3(oa.blocks + ob.blocks, nb), 256, 0, st>>>(oa, ob, K, kx);
+                 on_b ? ks_mode : 0, -1, Bs, slB, exB, Nc, (rowsB + kSV - 1) / kSV};
+    k_oz_split<<<dim3(oa.blocks + ob.blocks, nb), 256, oz_split_smem(K), st>>>(oa, ob, K, kx);
     OzMmaArgs m;
     m.As = As; m.sAs = slA; m.exA = exA; m.sExA = M;
     m.Bs = Bs; m.sBs = slB; m.exB = exB; m.sExB = Nc;
