@@ -530,16 +530,17 @@ __global__ void __launch_bounds__(256) k_oz_mma(OzMmaArgs a) {
 // ---------------------------------------------------------------------------
 // Fused product: the digit slices are cut by the CTA itself, straight into
 // the shared-memory stage the tensor cores read, so no slice makes a round
-// trip through global memory and no split kernel runs.  256 threads: all of
-// them split (the 128 rows of op(A) and BN columns of op(B) of the tile, one
-// K chunk of 32 at a time, two stages), thread 0 also issues the MMAs of a
-// chunk once every thread has arrived on the stage's `full` barrier (each
-// after a proxy fence that makes its shared-memory writes visible to the
-// tensor cores); splitting chunk c + 1 overlaps the MMAs of chunk c.
-// Before the K loop the CTA finds the exponent of every row of op(A) and
-// column of op(B) of its tile over the whole K range (the digit alignment).
-// Memory access follows the operand's layout: a vector contiguous along k is
-// read by lanes along k, otherwise lanes run along the vectors.
+// trip through global memory and no split kernel runs.  288 threads: the
+// kFT = 256 threads of warps 0-7 split (the 128 rows of op(A) and BN columns
+// of op(B) of the tile, one K chunk of 32 at a time, two stages) and arrive
+// on the stage's `full` barrier, each after a proxy fence that makes its
+// shared-memory writes visible to the tensor cores; one thread of warp 8
+// issues the MMAs of the chunk, so splitting chunk c + 1 overlaps the MMAs of
+// chunk c.  Before the K loop the split threads find the exponent of every
+// row of op(A) and column of op(B) of the tile over the whole K range (the
+// digit alignment).  Memory access follows the operand's layout: a vector
+// contiguous along k is read by lanes along k, otherwise lanes run along the
+// vectors.
 // ---------------------------------------------------------------------------
 struct OzFusedArgs {
   const double* A; long long sA, a_sv, a_sk;
@@ -556,20 +557,76 @@ struct OzFusedArgs {
 
 constexpr int kFT = 256;  // threads of the fused kernel
 
-// Exponent (unbiased, plus the balance offset) of the largest element of
-// vector v of an operand over k < K; -100000 for a zero vector.
-__device__ __forceinline__ int oz_vec_emax_lanes_k(const double* M, long long sv, long long sk, int v,
-                                                  int K, const double* kss, const int* kev,
-                                                  int ksign, bool scaled, int lane) {
-  int emax = -100000;
-  for (int k = lane; k < K; k += 32) {
-    double x = M[v * sv + k * sk];
-    if (scaled) x *= kss[k];
-    const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
-    if (E != 0) emax = max(emax, E - 1023 + ksign * kev[k]);
+// ex_s[r] = (exponent, unbiased, plus the balance offset ksign kev[k], of the
+// largest element of vector v0 + r of an operand over k < K) - 6, for the R
+// vectors of a tile; -100006 for a zero or missing vector.  The kFT split
+// threads take part; every thread has several loads in flight before it
+// reduces (the pass is latency-bound otherwise).  A vector contiguous along k
+// is read by a warp along k, four vectors at a time; otherwise lanes run
+// along the vectors and the threads split the k range, combined with shared
+// atomics.  Ends with a barrier of the split threads.
+// Barrier of the kFT split threads only (named barrier 1).
+__device__ __forceinline__ void oz_split_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kFT) : "memory"); }
+
+__device__ __forceinline__ int oz_elem_exp(double x, int kv) {
+  const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
+  return (E != 0) ? E - 1023 + kv : -100000;
+}
+
+__device__ void oz_tile_emax(const double* Mp, long long sv, long long sk, int v0, int nvec, int R,
+                             int K, const double* kss, const int* kev, int ksign, bool scaled,
+                             int* ex_s) {
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  constexpr int nw = kFT / 32;
+  if (sk == 1) {
+    for (int r0 = warp * 4; r0 < R; r0 += 4 * nw) {
+      int em[4] = {-100000, -100000, -100000, -100000};
+      for (int k = lane; k < K; k += 32) {
+        double x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + r0 + u;
+          x[u] = (r0 + u < R && v < nvec) ? Mp[v * sv + k] : 0.0;
+        }
+        const double kf = scaled ? kss[k] : 1.0;
+        const int kv = ksign * kev[k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) em[u] = max(em[u], oz_elem_exp(scaled ? x[u] * kf : x[u], kv));
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        for (int q = 16; q > 0; q >>= 1) em[u] = max(em[u], __shfl_xor_sync(0xFFFFFFFFu, em[u], q));
+        if (lane == 0 && r0 + u < R) ex_s[r0 + u] = em[u] - 6;
+      }
+    }
+    oz_split_sync();
+  } else {
+    for (int r = t; r < R; r += kFT) ex_s[r] = -100000;
+    oz_split_sync();
+    const int tpv = kFT / R;  // threads per vector (R divides kFT)
+    const int r = t % R, ks0 = t / R, v = v0 + r;
+    int em = -100000;
+    if (v < nvec) {
+      constexpr int kU = 8;
+      for (int k0 = ks0; k0 < K; k0 += tpv * kU) {
+        double x[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int k = k0 + u * tpv;
+          x[u] = (k < K) ? Mp[v * sv + k * sk] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int k = k0 + u * tpv;
+          if (k < K) em = max(em, oz_elem_exp(scaled ? x[u] * kss[k] : x[u], ksign * kev[k]));
+        }
+      }
+    }
+    atomicMax(&ex_s[r], em);
+    oz_split_sync();
+    for (int q = t; q < R; q += kFT) ex_s[q] -= 6;
+    oz_split_sync();
   }
-  for (int q = 16; q > 0; q >>= 1) emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, q));
-  return emax;
 }
 
 // The 8 digit slices of elements k0 .. k0 + 7 of vector v (already scaled;
@@ -665,13 +722,13 @@ constexpr int kUnitsPerThread = 3;
 __device__ __forceinline__ void oz_split_chunk2(const OzOperand& oa, const OzOperand& ob, int K,
                                                 int kc, const double* kss, const int* kev) {
   const int ua = oa.R * (kTK / 8), ub = ob.R * (kTK / 8), total = ua + ub;
-  for (int base = 0; base < total; base += kUnitsPerThread * static_cast<int>(blockDim.x)) {
+  for (int base = 0; base < total; base += kUnitsPerThread * kFT) {
     double x[kUnitsPerThread][8];
     int vv[kUnitsPerThread], kgs[kUnitsPerThread];
     bool isA[kUnitsPerThread], live[kUnitsPerThread];
 #pragma unroll
     for (int t = 0; t < kUnitsPerThread; ++t) {
-      const int u = base + t * static_cast<int>(blockDim.x) + static_cast<int>(threadIdx.x);
+      const int u = base + t * kFT + static_cast<int>(threadIdx.x);
       live[t] = u < total;
       isA[t] = u < ua;
       const OzOperand& o = isA[t] ? oa : ob;
@@ -704,7 +761,7 @@ __device__ __forceinline__ void oz_split_chunk2(const OzOperand& oa, const OzOpe
 }
 
 template <int BN>
-__global__ void __launch_bounds__(kFT, 1) k_oz_fused(OzFusedArgs a) {
+__global__ void __launch_bounds__(kFT + 32, 1) k_oz_fused(OzFusedArgs a) {
   using Tl = OzTile<BN>;
   extern __shared__ __align__(1024) unsigned char oz_sm[];
   __shared__ uint64_t full[kStages], mmad[kStages];
@@ -744,47 +801,11 @@ __global__ void __launch_bounds__(kFT, 1) k_oz_fused(OzFusedArgs a) {
     kev_s[k] = a.kexp ? a.kexp[b * static_cast<long long>(K) + k] : 0;
   }
   __syncthreads();
-  // exponents of the tile's rows of op(A) and columns of op(B)
-  auto vec_emax = [&](const double* Mp, long long sv, long long sk, int v, int nvec, int ksign,
-                      bool sc) -> int {
-    if (v >= nvec) return -100000;
-    return oz_vec_emax_lanes_k(Mp, sv, sk, v, K, ks_s, kev_s, ksign, sc, lane);
-  };
-  if (a.a_sk == 1) {
-    for (int v = warp; v < kTM; v += nw) {
-      const int e = vec_emax(A, a.a_sv, a.a_sk, i0 + v, M, 1, scA);
-      if (lane == 0) exA_s[v] = e - 6;
-    }
-  } else {
-    for (int v = threadIdx.x; v < kTM; v += blockDim.x) {
-      int emax = -100000;
-      if (i0 + v < M)
-        for (int k = 0; k < K; ++k) {
-          double x = A[(i0 + v) * a.a_sv + k * a.a_sk];
-          if (scA) x *= ks_s[k];
-          const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
-          if (E != 0) emax = max(emax, E - 1023 + kev_s[k]);
-        }
-      exA_s[v] = emax - 6;
-    }
-  }
-  if (a.b_sk == 1) {
-    for (int v = warp; v < BN; v += nw) {
-      const int e = vec_emax(B, a.b_sv, a.b_sk, j0 + v, Nc, -1, scB);
-      if (lane == 0) exB_s[v] = e - 6;
-    }
-  } else {
-    for (int v = threadIdx.x; v < BN; v += blockDim.x) {
-      int emax = -100000;
-      if (j0 + v < Nc)
-        for (int k = 0; k < K; ++k) {
-          double x = B[(j0 + v) * a.b_sv + k * a.b_sk];
-          if (scB) x *= ks_s[k];
-          const int E = static_cast<int>((__double_as_longlong(x) >> 52) & 0x7FF);
-          if (E != 0) emax = max(emax, E - 1023 - kev_s[k]);
-        }
-      exB_s[v] = emax - 6;
-    }
+  // exponents of the tile's rows of op(A) and columns of op(B) (split
+  // threads; the MMA warp waits at the barrier below)
+  if (threadIdx.x < kFT) {
+    oz_tile_emax(A, a.a_sv, a.a_sk, i0, M, kTM, K, ks_s, kev_s, 1, scA, exA_s);
+    oz_tile_emax(B, a.b_sv, a.b_sk, j0, Nc, BN, K, ks_s, kev_s, -1, scB, exB_s);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -798,47 +819,56 @@ __global__ void __launch_bounds__(kFT, 1) k_oz_fused(OzFusedArgs a) {
     colx[q] = exB_s[q];
   }
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((BN >> 3) << 17) | ((kTM >> 4) << 24);
-  int committed = -1;  // thread 0: last chunk whose MMAs were committed
-  for (int c = 0; c < nkc; ++c) {
-    const int st = c & 1;
-    unsigned char* smA = oz_sm + st * Tl::kStage;
-    unsigned char* smB = smA + kS * kATile;
-    if (c >= 2 && !mbar_wait(&mmad[st], ((c - 2) >> 1) & 1)) fail_sh = 1;
-    if (*reinterpret_cast<volatile int*>(&fail_sh)) break;
-    const OzOperand oa{A, a.a_sv, a.a_sk, i0, M, kTM, 1, scA, exA_s, smA};
-    const OzOperand ob{B, a.b_sv, a.b_sk, j0, Nc, BN, -1, scB, exB_s, smB};
-    oz_split_chunk2(oa, ob, K, c, ks_s, kev_s);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
-    if (threadIdx.x == 0) {
-      if (!mbar_wait(&full[st], (c >> 1) & 1)) {
-        fail_sh = 1;
-      } else {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        for (int d = 0; d < kS; ++d)
-          for (int p = 0; p <= d; ++p) {
-            const int q = d - p;
-            for (int ks = 0; ks < kTK / 16; ++ks) {
-              const uint64_t ad = oz_desc(smem_u32(smA + p * kATile + ks * 256));
-              const uint64_t bd = oz_desc(smem_u32(smB + q * Tl::kBTile + ks * 256));
-              const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
-              asm volatile(
-                  "{\n .reg .pred pa;\n setp.ne.u32 pa, %4, 0;\n"
-                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tbase + d * BN),
-                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-            }
-          }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&mmad[st])));
-        committed = c;
-      }
+  volatile int* fail_v = &fail_sh;
+  if (threadIdx.x < kFT) {
+    // split threads: chunk c goes to stage c & 1 once the MMAs of chunk c - 2,
+    // which read that stage, are done
+    for (int c = 0; c < nkc; ++c) {
+      const int st = c & 1;
+      unsigned char* smA = oz_sm + st * Tl::kStage;
+      unsigned char* smB = smA + kS * kATile;
+      if (c >= kStages && !mbar_wait(&mmad[st], ((c - kStages) >> 1) & 1)) *fail_v = 1;
+      if (*fail_v) break;
+      const OzOperand oa{A, a.a_sv, a.a_sk, i0, M, kTM, 1, scA, exA_s, smA};
+      const OzOperand ob{B, a.b_sv, a.b_sk, j0, Nc, BN, -1, scB, exB_s, smB};
+      oz_split_chunk2(oa, ob, K, c, ks_s, kev_s);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
     }
+  } else if (threadIdx.x == kFT) {
+    // MMA issuer (warp 8): the split warps go on with the next chunk while
+    // this thread blocks on the MMA queue
+    int committed = -1;
+    for (int c = 0; c < nkc; ++c) {
+      const int st = c & 1;
+      if (*fail_v || !mbar_wait(&full[st], (c >> 1) & 1)) {
+        *fail_v = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      unsigned char* smA = oz_sm + st * Tl::kStage;
+      unsigned char* smB = smA + kS * kATile;
+      for (int d = 0; d < kS; ++d)
+        for (int p = 0; p <= d; ++p) {
+          const int q = d - p;
+          for (int ks = 0; ks < kTK / 16; ++ks) {
+            const uint64_t ad = oz_desc(smem_u32(smA + p * kATile + ks * 256));
+            const uint64_t bd = oz_desc(smem_u32(smB + q * Tl::kBTile + ks * 256));
+            const uint32_t acc = (c > 0 || p > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n .reg .pred pa;\n setp.ne.u32 pa, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pa;\n}" ::"r"(tbase + d * BN),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+          }
+        }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mmad[st])));
+      committed = c;
+    }
+    // the MMAs of the last committed chunk (commit tracks all earlier MMAs too)
+    if (committed >= 0 && !mbar_wait(&mmad[committed & 1], (committed >> 1) & 1)) *fail_v = 1;
+    if (committed != nkc - 1) *fail_v = 1;
   }
-  // the MMAs of the last committed chunk (commit tracks all earlier MMAs too)
-  if (threadIdx.x == 0 && committed >= 0 &&
-      !mbar_wait(&mmad[committed & 1], (committed >> 1) & 1))
-    fail_sh = 1;
-  if (threadIdx.x == 0 && committed != nkc - 1) fail_sh = 1;
   __syncthreads();
   const bool ok = *reinterpret_cast<volatile int*>(&fail_sh) == 0;
   if (!ok && threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
@@ -860,7 +890,8 @@ __global__ void __launch_bounds__(kFT, 1) k_oz_fused(OzFusedArgs a) {
     const int rowx = exA_s[rl];
     constexpr int kLd = BN + 1;
     double* stg = reinterpret_cast<double*>(oz_sm);
-    for (int c = half * (BN / 32); c < (half + 1) * (BN / 32); ++c) {
+    const int c_end = (warp < kFT / 32) ? (half + 1) * (BN / 32) : 0;  // the MMA warp: none
+    for (int c = half * (BN / 32); c < c_end; ++c) {
       uint32_t v[kS][16];
 #pragma unroll
       for (int d = 0; d < kS; ++d) {
@@ -945,7 +976,7 @@ cudaError_t oz_run_fused(const OzProduct& g, int batch, void* scratch, int max_b
     f.cs = g.cs ? g.cs + b0 * g.scs : nullptr; f.scs = g.scs; f.cs_mode = g.cs ? g.cs_mode : 0;
     f.alpha = g.alpha; f.beta = g.beta;
     f.status = status;
-    k_oz_fused<BN><<<dim3((Nc + BN - 1) / BN, (M + kTM - 1) / kTM, nb), kFT, smem, st>>>(f);
+    k_oz_fused<BN><<<dim3((Nc + BN - 1) / BN, (M + kTM - 1) / kTM, nb), kFT + 32, smem, st>>>(f);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
