@@ -530,11 +530,11 @@ __global__ void __launch_bounds__(256) k_oz_mma(OzMmaArgs a) {
 // ---------------------------------------------------------------------------
 // Fused product: the digit slices are cut by the CTA itself, straight into
 // the shared-memory stage the tensor cores read, so no slice makes a round
-// trip through global memory and no split kernel runs.  288 threads: the
-// kFT = 256 threads of warps 0-7 split (the 128 rows of op(A) and BN columns
+// trip through global memory and no split kernel runs.  544 threads: the
+// kFT = 512 threads of warps 0-15 split (the 128 rows of op(A) and BN columns
 // of op(B) of the tile, one K chunk of 32 at a time, two stages) and arrive
 // on the stage's `full` barrier, each after a proxy fence that makes its
-// shared-memory writes visible to the tensor cores; one thread of warp 8
+// shared-memory writes visible to the tensor cores; one thread of warp 16
 // issues the MMAs of the chunk, so splitting chunk c + 1 overlaps the MMAs of
 // chunk c.  Before the K loop the split threads find the exponent of every
 // row of op(A) and column of op(B) of the tile over the whole K range (the
@@ -555,7 +555,7 @@ struct OzFusedArgs {
   int* status;
 };
 
-constexpr int kFT = 256;  // threads of the fused kernel
+constexpr int kFT = 512;  // split (and epilogue) threads of the fused kernel
 
 // ex_s[r] = (exponent, unbiased, plus the balance offset ksign kev[k], of the
 // largest element of vector v0 + r of an operand over k < K) - 6, for the R
@@ -715,48 +715,48 @@ __device__ __forceinline__ void oz_unit_coords(const OzOperand& o, int u, int& v
   }
 }
 
-// Split K chunk kc of both operands into the stage: every thread takes up to
-// kUnitsPerThread units, loads all their elements first (independent loads
-// in flight), then cuts them.
-constexpr int kUnitsPerThread = 3;
+// Split K chunk kc of both operands into the stage: every split thread takes
+// up to kUnitsPerThread units (the (128 + BN) x 4 units of a chunk need at
+// most two per thread), loads all their elements first (independent loads in
+// flight), then cuts them.
+constexpr int kUnitsPerThread = 2;
+static_assert((kTM + 64) * (kTK / 8) <= kUnitsPerThread * kFT, "units of a chunk per thread");
 __device__ __forceinline__ void oz_split_chunk2(const OzOperand& oa, const OzOperand& ob, int K,
                                                 int kc, const double* kss, const int* kev) {
   const int ua = oa.R * (kTK / 8), ub = ob.R * (kTK / 8), total = ua + ub;
-  for (int base = 0; base < total; base += kUnitsPerThread * kFT) {
-    double x[kUnitsPerThread][8];
-    int vv[kUnitsPerThread], kgs[kUnitsPerThread];
-    bool isA[kUnitsPerThread], live[kUnitsPerThread];
+  double x[kUnitsPerThread][8];
+  int vv[kUnitsPerThread], kgs[kUnitsPerThread];
+  bool isA[kUnitsPerThread], live[kUnitsPerThread];
 #pragma unroll
-    for (int t = 0; t < kUnitsPerThread; ++t) {
-      const int u = base + t * kFT + static_cast<int>(threadIdx.x);
-      live[t] = u < total;
-      isA[t] = u < ua;
-      const OzOperand& o = isA[t] ? oa : ob;
-      int v = 0, kg = 0;
-      if (live[t]) oz_unit_coords(o, isA[t] ? u : u - ua, v, kg);
-      vv[t] = v;
-      kgs[t] = kg;
-      const int vg = o.v0 + v, k0 = kc * kTK + kg * 8;
+  for (int t = 0; t < kUnitsPerThread; ++t) {
+    const int u = t * kFT + static_cast<int>(threadIdx.x);
+    live[t] = u < total;
+    isA[t] = u < ua;
+    const OzOperand& o = isA[t] ? oa : ob;
+    int v = 0, kg = 0;
+    if (live[t]) oz_unit_coords(o, isA[t] ? u : u - ua, v, kg);
+    vv[t] = v;
+    kgs[t] = kg;
+    const int vg = o.v0 + v, k0 = kc * kTK + kg * 8;
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = k0 + e;
-        x[t][e] = (live[t] && vg < o.nvec && k < K) ? o.M[vg * o.sv + k * o.sk] : 0.0;
-      }
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      x[t][e] = (live[t] && vg < o.nvec && k < K) ? o.M[vg * o.sv + k * o.sk] : 0.0;
     }
+  }
 #pragma unroll
-    for (int t = 0; t < kUnitsPerThread; ++t) {
-      if (!live[t]) continue;
-      const OzOperand& o = isA[t] ? oa : ob;
-      const int k0 = kc * kTK + kgs[t] * 8;
-      int kv[8];
+  for (int t = 0; t < kUnitsPerThread; ++t) {
+    if (!live[t]) continue;
+    const OzOperand& o = isA[t] ? oa : ob;
+    const int k0 = kc * kTK + kgs[t] * 8;
+    int kv[8];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int k = k0 + e;
-        kv[e] = (k < K) ? o.ksign * kev[k] : 0;
-        if (o.scaled && k < K) x[t][e] *= kss[k];
-      }
-      oz_split_unit(x[t], kv, o.ex[vv[t]] + 6, o.op, o.R, vv[t], kgs[t]);  // ex holds emax - 6
+    for (int e = 0; e < 8; ++e) {
+      const int k = k0 + e;
+      kv[e] = (k < K) ? o.ksign * kev[k] : 0;
+      if (o.scaled && k < K) x[t][e] *= kss[k];
     }
+    oz_split_unit(x[t], kv, o.ex[vv[t]] + 6, o.op, o.R, vv[t], kgs[t]);  // ex holds emax - 6
   }
 }
 
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(kFT + 32, 1) k_oz_fused(OzFusedArgs a) {
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[st])) : "memory");
     }
   } else if (threadIdx.x == kFT) {
-    // MMA issuer (warp 8): the split warps go on with the next chunk while
+    // MMA issuer (warp 16): the split warps go on with the next chunk while
     // this thread blocks on the MMA queue
     int committed = -1;
     for (int c = 0; c < nkc; ++c) {
@@ -874,9 +874,10 @@ __global__ void __launch_bounds__(kFT + 32, 1) k_oz_fused(OzFusedArgs a) {
   if (!ok && threadIdx.x == 0) atomicExch(a.status, kDevTimeout);
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // Recombination as in k_oz_mma: warps w and w + 4 share the TMEM lanes of
-    // quarter w % 4, each taking half of the columns; staged through shared
-    // memory for row-wise access to C.
+    // Recombination as in k_oz_mma: the kFT / 128 warps w = q, q + 4, ...
+    // share the TMEM lanes of quarter q, each taking an equal part of the
+    // columns; staged through shared memory for row-wise access to C.
+    constexpr int kGroups = kFT / 128;  // warps sharing the TMEM lanes of one quarter
     const int quarter = warp & 3, half = warp >> 2;
     const int rl = quarter * 32 + lane;
     const int i = i0 + rl;
@@ -890,24 +891,25 @@ __global__ void __launch_bounds__(kFT + 32, 1) k_oz_fused(OzFusedArgs a) {
     const int rowx = exA_s[rl];
     constexpr int kLd = BN + 1;
     double* stg = reinterpret_cast<double*>(oz_sm);
-    const int c_end = (warp < kFT / 32) ? (half + 1) * (BN / 32) : 0;  // the MMA warp: none
-    for (int c = half * (BN / 32); c < c_end; ++c) {
-      uint32_t v[kS][16];
+    // eight columns at a time (64 accumulator registers), so that several
+    // elements' integer chains are in flight per thread
+    constexpr int kCg = BN / 8 / kGroups;  // 8-column groups per warp
+    const int c_end = (warp < kFT / 32) ? (half + 1) * kCg : 0;  // the MMA warp: none
+    for (int c = half * kCg; c < c_end; ++c) {
+      uint32_t v[kS][8];
 #pragma unroll
       for (int d = 0; d < kS; ++d) {
-        const uint32_t ta = tbase + (static_cast<uint32_t>(quarter * 32) << 16) + d * BN + c * 16;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]), "=r"(v[d][5]),
-              "=r"(v[d][6]), "=r"(v[d][7]), "=r"(v[d][8]), "=r"(v[d][9]), "=r"(v[d][10]), "=r"(v[d][11]),
-              "=r"(v[d][12]), "=r"(v[d][13]), "=r"(v[d][14]), "=r"(v[d][15])
-            : "r"(ta));
+        const uint32_t ta = tbase + (static_cast<uint32_t>(quarter * 32) << 16) + d * BN + c * 8;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]),
+                       "=r"(v[d][5]), "=r"(v[d][6]), "=r"(v[d][7])
+                     : "r"(ta));
       }
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row_ok) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int jj = c * 16 + q;
+        for (int q = 0; q < 8; ++q) {
+          const int jj = c * 8 + q;
           long long hi = 0, lo = 0;
 #pragma unroll
           for (int d = 0; d < 4; ++d)
@@ -924,17 +926,25 @@ __global__ void __launch_bounds__(kFT + 32, 1) k_oz_fused(OzFusedArgs a) {
       }
     }
     __syncthreads();
+    // C = staged + beta C, row-wise (coalesced), eight loads of C in flight
+    // per thread before the first store
     double* C = a.C + b * a.sC;
-    for (int r = warp; r < kTM; r += nw) {
-      const int ii = i0 + r;
-      if (ii >= M) break;
-      for (int jj = lane; jj < BN; jj += 32) {
-        const int j = j0 + jj;
-        if (j < Nc) {
-          const size_t o = static_cast<size_t>(ii) * a.ldc + j;
+    const int rows = min(kTM, M - i0), tot = rows * BN;
+    constexpr int kU = 8;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += kU * blockDim.x) {
+      double cv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x, r = e / BN, jj = e - r * BN, j = j0 + jj;
+        cv[u] = (a.beta != 0.0 && e < tot && j < Nc) ? C[static_cast<size_t>(i0 + r) * a.ldc + j] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x, r = e / BN, jj = e - r * BN, j = j0 + jj;
+        if (e < tot && j < Nc) {
           double val = stg[r * kLd + jj];
-          if (a.beta != 0.0) val = fma(a.beta, C[o], val);
-          C[o] = val;
+          if (a.beta != 0.0) val = fma(a.beta, cv[u], val);
+          C[static_cast<size_t>(i0 + r) * a.ldc + j] = val;
         }
       }
     }
