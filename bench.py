@@ -625,12 +625,18 @@ def run_config(args):
     for prec in precs:
         groups = config_groups(pkg, args.config, prec)
         tuned = None
+        tiles = None
         if args.autotune > 0 and args.config in ("c2", "c4"):
             t0 = time.perf_counter()
             groups = pkg.autotune(groups, drift_target=args.autotune)
+            tiles = pkg.autotune_tiles(groups)
             tuned = {"target": args.autotune, "seconds": time.perf_counter() - t0,
-                     "n_s": [g.stab_interval for g in groups], "k": [g.delay_k for g in groups]}
+                     "n_s": [g.stab_interval for g in groups], "k": [g.delay_k for g in groups],
+                     "tiles": tiles}
         with pkg.DQMC(groups, seed=0) as sim:
+            if tiles:
+                for gi, t in enumerate(tiles):
+                    sim.set_tiles(gi, **t)
             n_up = sum(g.n_chains * g.N * g.L for g in groups)
             gbuf = torch.empty(int(pkg.lib().dqmc_gtau_size(sim._h)), dtype=torch.float64, device="cuda")
             dt = torch.empty(sim.n_chains, dtype=torch.float64, device="cuda")
