@@ -176,6 +176,18 @@ __device__ __forceinline__ void peer_barrier(uint64_t* bars, int cs, int rank, i
 // Threads per column of G: two for float pairs (one computes the column and
 // one the row correction of an accepted flip, and they split the rows of the
 // flush), one otherwise.
+// Columns of G staged in shared memory per window of sites (k_metropolis).
+constexpr int kWin = 32;
+
+// Pending updates per register chunk of the flush: all of them for one
+// thread per column; eight for float pairs, whose two threads per column
+// each fold eight rows at a time (more independent sums in flight at the
+// 128-register limit of 512 threads).
+template <typename T>
+constexpr int kFlushMC() {
+  return std::is_same<T, df32>::value ? 8 : kMaxDelay;
+}
+
 template <typename T>
 constexpr int metro_halves() {
   return std::is_same<T, df32>::value ? 2 : 1;
@@ -231,6 +243,7 @@ __global__ void __launch_bounds__(256 * metro_halves<T>()) k_metropolis(T* Gall,
   T* d = V + a.k * NP;                              // [NP] diag of G_cur
   float* df = reinterpret_cast<float*>(d + NP);     // [NP] diag of G_cur, rounded to float
   int* ss = reinterpret_cast<int*>(df + NP);        // [NP] field of the slice
+  T* cw = reinterpret_cast<T*>(ss + NP);            // [kWin][NP + 1] window of columns of G
 
   const uint32_t sweep = *a.sweep_ctr;
   if (act && h == 0) {
@@ -247,42 +260,58 @@ __global__ void __launch_bounds__(256 * metro_halves<T>()) k_metropolis(T* Gall,
   }
   __syncthreads();
 
-  // Column i and row i of G for the next kPre sites, loaded ahead (a flush
-  // rewrites G, after which the window is reloaded).
-  // With two threads per column each half keeps only its own vector (pr is
-  // then unused and stays empty).
-  constexpr int kPre = 4;
-  T pc[kPre], pr[kH == 1 ? kPre : 1];
-  // G[j][q] for the column half (or single thread), G[q][j] for the row half
-  auto ld_c = [&](int q) -> T {
-    if (!act || q >= N) return T(0);
-    return (kH == 1 || h == 0) ? G[static_cast<size_t>(j) * N + q] : G[static_cast<size_t>(q) * N + j];
+  // Columns wb .. wb + kWin - 1 of G in shared memory, cw[c][j] = G[j][wb + c]:
+  // loaded with whole-row segments (a column of the row-major G would take one
+  // memory transaction per row), reloaded every kWin sites and after a flush.
+  const int ldw = NP + 1;  // odd stride in 8-byte words: conflict-free transposed stores
+  auto load_window = [&](int wb) {
+    constexpr int kU = 8;
+    const int tot = N * kWin;
+    for (int e0 = threadIdx.x; e0 < tot; e0 += kU * blockDim.x) {
+      T t[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x, r = e / kWin, c = e - r * kWin;
+        t[u] = (e < tot && wb + c < N) ? G[static_cast<size_t>(r) * N + wb + c] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x, r = e / kWin, c = e - r * kWin;
+        if (e < tot) cw[c * ldw + r] = t[u];
+      }
+    }
   };
+  int wb = 0;
+  load_window(0);
+  __syncthreads();
+  // Row i of G for the next kPre sites, loaded ahead into registers (rows
+  // are contiguous; a flush rewrites G, after which the window is reloaded).
+  // With two threads per column only the row half uses it.
+  constexpr int kPre = 4;
+  T pr[kPre];
   auto ld_r = [&](int q) -> T {
-    return (act && q < N) ? G[static_cast<size_t>(q) * N + j] : T(0);
+    return (act && q < N && (kH == 1 || h == 1)) ? G[static_cast<size_t>(q) * N + j] : T(0);
   };
 #pragma unroll
-  for (int q = 0; q < kPre; ++q) {
-    pc[q] = ld_c(q);
-    if constexpr (kH == 1) pr[q] = ld_r(q);
-  }
+  for (int q = 0; q < kPre; ++q) pr[q] = ld_r(q);
   int cnt = 0;
   unsigned naccept = 0;
   // The field is written back after the slice: a peer CTA of the cluster may
   // still be reading the slice's initial field when this one accepts a flip.
   bool flip = false;
   for (int i = 0; i < N; ++i) {
-    // kH == 2: colv is G[j][i] for h = 0 and G[i][j] for h = 1
-    const T colv = pc[0];
-    const T rowv = (kH == 1) ? pr[0] : pc[0];
-#pragma unroll
-    for (int q = 0; q + 1 < kPre; ++q) {
-      pc[q] = pc[q + 1];
-      if constexpr (kH == 1) pr[q] = pr[q + 1];
+    if (i == wb + kWin) {  // every warp is past site i - 1
+      __syncthreads();
+      wb = i;
+      load_window(wb);
+      __syncthreads();
     }
-    const int inext = i + kPre;
-    pc[kPre - 1] = ld_c(inext);
-    if constexpr (kH == 1) pr[kPre - 1] = ld_r(inext);
+    // kH == 2: colv is G[j][i] for h = 0 and rowv G[i][j] for h = 1
+    const T colv = act ? cw[(i - wb) * ldw + j] : T(0);
+    const T rowv = pr[0];
+#pragma unroll
+    for (int q = 0; q + 1 < kPre; ++q) pr[q] = pr[q + 1];
+    pr[kPre - 1] = ld_r(i + kPre);
     // Decision u < R_up R_dn with R_up = 1 + D_up (1 - G_ii), R_dn = 1 + D_dn G_ii
     // (G_dn,ii = 1 - G_up,ii).  Lane 0 of every warp takes it in FP32 unless u
     // lies within 1e-4 of R, where it is retaken in FP64; all warps agree
@@ -361,23 +390,23 @@ __global__ void __launch_bounds__(256 * metro_halves<T>()) k_metropolis(T* Gall,
       ++cnt;
       if (cnt == a.k) {
         if (cs > 1) peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
-        delayed_flush<T, 8 / kH, kMaxDelay / kH>(G, U, V, cnt, N, NP, j, ra, rb);
+        delayed_flush<T, 8, kFlushMC<T>()>(G, U, V, cnt, N, NP, j, ra, rb);
         cnt = 0;
         if (cs > 1)
           peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
         else
           __syncthreads();
+        wb = i + 1;
+        load_window(wb);
+        __syncthreads();
 #pragma unroll
-        for (int q = 0; q < kPre; ++q) {
-          pc[q] = ld_c(i + 1 + q);
-          if constexpr (kH == 1) pr[q] = ld_r(i + 1 + q);
-        }
+        for (int q = 0; q < kPre; ++q) pr[q] = ld_r(i + 1 + q);
       }
     }
   }
   if (cnt > 0) {
     if (cs > 1) peer_barrier(xbar, cs, rank, xphase, a.status, &xbroken);
-    delayed_flush<T, 8 / kH, kMaxDelay / kH>(G, U, V, cnt, N, NP, j, ra, rb);
+    delayed_flush<T, 8, kFlushMC<T>()>(G, U, V, cnt, N, NP, j, ra, rb);
   }
   // No CTA leaves while a peer may still arrive on its barrier or read the
   // slice's field.
@@ -781,7 +810,8 @@ template <typename T>
 size_t metropolis_smem(int N, int k) {
   const int NP = ((N + 31) / 32) * 32;
   return static_cast<size_t>(NP) * (sizeof(double) + sizeof(float)) + 2ull * k * NP * sizeof(T) +
-         static_cast<size_t>(NP) * (sizeof(T) + sizeof(float) + sizeof(int));
+         static_cast<size_t>(NP) * (sizeof(T) + sizeof(float) + sizeof(int)) +
+         static_cast<size_t>(kWin) * (NP + 1) * sizeof(T);
 }
 
 template <typename T>
