@@ -433,30 +433,44 @@ __device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int vi = e / N, i = e - vi * N;
+  // A thread takes the same element of two vectors (2 vp, 2 vp + 1): the two
+  // sums are independent and share every tap load.  The taps are stored twice
+  // over (tx[k] = Ex[k mod Lx] for k < 2 Lx), so that tap x - x' mod Lx is
+  // tx[x + Lx - x'] without a wrap test.
+  const int npair = (nv + 1) >> 1, ptot = npair * N;
+  for (int e = threadIdx.x; e < ptot; e += blockDim.x) {
+    const int vp = e / N, i = e - vp * N;
     const int x = i % Lx, y = i / Lx;
-    const T* row = v + vi * ld + Lx * y;
-    ProdSum<T> acc;
+    const bool two = 2 * vp + 1 < nv;
+    const T* row0 = v + (2 * vp) * ld + Lx * y;
+    const T* row1 = two ? row0 + ld : row0;
+    const T* tp = tx + x + Lx;
+    ProdSum<T> a0, a1;
     for (int xp = 0; xp < Lx; ++xp) {
-      int dd = x - xp;
-      dd += dd < 0 ? Lx : 0;
-      acc.add(tx[dd], row[xp]);
+      const T t = tp[-xp];
+      a0.add(t, row0[xp]);
+      a1.add(t, row1[xp]);
     }
-    tmp[vi * ld + i] = acc.get();
+    tmp[(2 * vp) * ld + i] = a0.get();
+    if (two) tmp[(2 * vp + 1) * ld + i] = a1.get();
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int vi = e / N, i = e - vi * N;
+  for (int e = threadIdx.x; e < ptot; e += blockDim.x) {
+    const int vp = e / N, i = e - vp * N;
     const int x = i % Lx, y = i / Lx;
-    const T* col = tmp + vi * ld + x;
-    ProdSum<T> acc;
+    const bool two = 2 * vp + 1 < nv;
+    const T* col0 = tmp + (2 * vp) * ld + x;
+    const T* col1 = two ? col0 + ld : col0;
+    const T* tp = ty + y + Ly;
+    ProdSum<T> a0, a1;
     for (int yp = 0; yp < Ly; ++yp) {
-      int dd = y - yp;
-      dd += dd < 0 ? Ly : 0;
-      acc.add(ty[dd], col[Lx * yp]);
+      const T t = tp[-yp];
+      a0.add(t, col0[Lx * yp]);
+      a1.add(t, col1[Lx * yp]);
     }
-    v[vi * ld + i] = post ? acc.get() * post[i] : acc.get();
+    const T sc = post ? post[i] : T(1);
+    v[(2 * vp) * ld + i] = post ? a0.get() * sc : a0.get();
+    if (two) v[(2 * vp + 1) * ld + i] = post ? a1.get() * sc : a1.get();
   }
   __syncthreads();
 }
@@ -477,8 +491,8 @@ __device__ __forceinline__ KronStage<T> kron_stage(unsigned char* raw, int nv, i
   s.v = reinterpret_cast<T*>(raw);
   s.tmp = s.v + nv * ld;
   s.tx = s.tmp + nv * ld;
-  s.ty = s.tx + kMaxSide;
-  s.sc = s.ty + kMaxSide;
+  s.ty = s.tx + 2 * kMaxSide;
+  s.sc = s.ty + 2 * kMaxSide;
   return s;
 }
 
@@ -500,11 +514,11 @@ __device__ __forceinline__ bool kron_entry_range(const KronArgs& a, int b, int* 
 
 template <typename T>
 __device__ __forceinline__ void kron_load_taps(const KronArgs& a, KronStage<T> s) {
-  if (threadIdx.x < kMaxSide) {
-    const int t = threadIdx.x;
+  if (threadIdx.x < 2 * kMaxSide) {  // each circulant row twice over (kron_transform)
+    const int t = threadIdx.x, tx = t % a.Lx, ty = t % a.Ly;
     const bool inv = (a.kind == kBIT);
-    s.tx[t] = static_cast<T>(inv ? a.taps.exi[t] : a.taps.ex[t]);
-    s.ty[t] = static_cast<T>(inv ? a.taps.eyi[t] : a.taps.ey[t]);
+    s.tx[t] = static_cast<T>(inv ? a.taps.exi[tx] : a.taps.ex[tx]);
+    s.ty[t] = static_cast<T>(inv ? a.taps.eyi[ty] : a.taps.ey[ty]);
   }
 }
 
@@ -843,7 +857,7 @@ cudaError_t launch_metropolis(T* G, int8_t* field, int C, const MetroArgs& a, cu
 
 template <typename T>
 size_t kron_smem(int N, int nv) {
-  return (2ull * nv * (N + 1) + 2 * kMaxSide + N) * sizeof(T);
+  return (2ull * nv * (N + 1) + 4 * kMaxSide + N) * sizeof(T);
 }
 
 template <typename T>
