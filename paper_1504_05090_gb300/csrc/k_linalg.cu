@@ -412,23 +412,22 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
   const int nrows = min(nv, N - r0);
   const int lo = a.cp[blk], hi = a.cp[blk + 1];
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  double* sbin = reinterpret_cast<double*>(sm_raw);
-  T* v = reinterpret_cast<T*>(sbin + N);
+  T* v = reinterpret_cast<T*>(sm_raw);
   T* tmp = v + nv * ld;
   T* tx = tmp + nv * ld;
-  T* ty = tx + kMaxSide;
-  T* sc = ty + kMaxSide;
+  T* ty = tx + 2 * kMaxSide;
+  T* sc = ty + 2 * kMaxSide;
   const bool inv = (a.kind == kBIT);
-  if (threadIdx.x < kMaxSide) {
-    tx[threadIdx.x] = static_cast<T>(inv ? a.taps.exi[threadIdx.x] : a.taps.ex[threadIdx.x]);
-    ty[threadIdx.x] = static_cast<T>(inv ? a.taps.eyi[threadIdx.x] : a.taps.ey[threadIdx.x]);
+  if (threadIdx.x < 2 * kMaxSide) {  // each circulant row twice over (kron_transform_d)
+    const int t = threadIdx.x, tx_ = t % a.Lx, ty_ = t % a.Ly;
+    tx[t] = static_cast<T>(inv ? a.taps.exi[tx_] : a.taps.ex[tx_]);
+    ty[t] = static_cast<T>(inv ? a.taps.eyi[ty_] : a.taps.ey[ty_]);
   }
   double* X = Xall + static_cast<size_t>(b) * a.mat_stride;
   for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
     const int vi = e / N, i = e - vi * N;
     v[vi * ld + i] = static_cast<T>(X[static_cast<size_t>(r0 + vi) * N + i]);
   }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) sbin[i] = 0.0;
   const Geom g{a.Lx, a.Ly, N};
   const int8_t* f = a.field + static_cast<size_t>(chain) * a.L * N;
   const T up = static_cast<T>(inv ? a.emc : a.ec), dn = static_cast<T>(inv ? a.ec : a.emc);
@@ -440,17 +439,22 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
       __syncthreads();
       kron_transform_d<T>(v, tmp, nrows, ld, a.Lx, a.Ly, N, tx, ty, sc, nullptr);
     }
-    for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
-      const int vi = e / N, el = e - vi * N;
-      const int q = r0 + vi;
-      const int sep = a.vec_is_col ? sep_index(el, q, g) : sep_index(q, el, g);
-      atomicAdd(&sbin[sep], to_d(v[vi * ld + el]));
-    }
-    __syncthreads();
+    // every vector has exactly one element per separation r: the thread of
+    // bin r sums them over the block's vectors in the working precision and
+    // adds the block's sum to the global bin
     double* out = a.bins + ((static_cast<size_t>(chain) * (a.L + 1) + l) * 2 + a.bin_slot) * N;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      atomicAdd(&out[i], sbin[i]);
-      sbin[i] = 0.0;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) {
+      const int rx = r % a.Lx, ry = r / a.Lx;
+      T acc = T(0);
+      for (int vi = 0; vi < nrows; ++vi) {
+        const int q = r0 + vi, qx = q % a.Lx, qy = q / a.Lx;
+        // vec_is_col: r = r_el - r_q, else r = r_q - r_el
+        const int ex = a.vec_is_col ? qx + rx : qx - rx + a.Lx;
+        const int ey = a.vec_is_col ? qy + ry : qy - ry + a.Ly;
+        const int el = (ex % a.Lx) + a.Lx * (ey % a.Ly);
+        acc = acc + v[vi * ld + el];
+      }
+      atomicAdd(&out[r], to_d(acc));
     }
   }
 }
@@ -466,30 +470,41 @@ __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, i
     }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int vi = e / N, i = e - vi * N;
+  // Two vectors per thread sharing each tap load; taps stored twice over
+  // (tx[k] = Ex[k mod Lx] for k < 2 Lx), tap x - x' mod Lx = tx[x + Lx - x'].
+  const int npair = (nv + 1) >> 1, ptot = npair * N;
+  for (int e = threadIdx.x; e < ptot; e += blockDim.x) {
+    const int vp = e / N, i = e - vp * N;
     const int x = i % Lx, y = i / Lx;
-    const T* row = v + vi * ld + Lx * y;
-    ProdSum<T> acc;
+    const bool two = 2 * vp + 1 < nv;
+    const T* row0 = v + (2 * vp) * ld + Lx * y;
+    const T* row1 = two ? row0 + ld : row0;
+    const T* tp = tx + x + Lx;
+    ProdSum<T> a0, a1;
     for (int xp = 0; xp < Lx; ++xp) {
-      int dd = x - xp;
-      dd += dd < 0 ? Lx : 0;
-      acc.add(tx[dd], row[xp]);
+      const T t = tp[-xp];
+      a0.add(t, row0[xp]);
+      a1.add(t, row1[xp]);
     }
-    tmp[vi * ld + i] = acc.get();
+    tmp[(2 * vp) * ld + i] = a0.get();
+    if (two) tmp[(2 * vp + 1) * ld + i] = a1.get();
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-    const int vi = e / N, i = e - vi * N;
+  for (int e = threadIdx.x; e < ptot; e += blockDim.x) {
+    const int vp = e / N, i = e - vp * N;
     const int x = i % Lx, y = i / Lx;
-    const T* col = tmp + vi * ld + x;
-    ProdSum<T> acc;
+    const bool two = 2 * vp + 1 < nv;
+    const T* col0 = tmp + (2 * vp) * ld + x;
+    const T* col1 = two ? col0 + ld : col0;
+    const T* tp = ty + y + Ly;
+    ProdSum<T> a0, a1;
     for (int yp = 0; yp < Ly; ++yp) {
-      int dd = y - yp;
-      dd += dd < 0 ? Ly : 0;
-      acc.add(ty[dd], col[Lx * yp]);
+      const T t = tp[-yp];
+      a0.add(t, col0[Lx * yp]);
+      a1.add(t, col1[Lx * yp]);
     }
-    v[vi * ld + i] = post ? acc.get() * post[i] : acc.get();
+    v[(2 * vp) * ld + i] = post ? a0.get() * post[i] : a0.get();
+    if (two) v[(2 * vp + 1) * ld + i] = post ? a1.get() * post[i] : a1.get();
   }
   __syncthreads();
 }
@@ -598,8 +613,8 @@ template cudaError_t launch_convert<df32>(const double*, df32*, long long, cudaS
 
 template <typename T>
 static cudaError_t gtau_launch(double* X, int batch, const GtauArgs& a, cudaStream_t st) {
-  const size_t sm = a.N * sizeof(double) +
-                    (2ull * a.nv * (a.N + 1) + 2 * kMaxSide + static_cast<size_t>(a.N)) * sizeof(T);
+  const size_t sm =
+                    (2ull * a.nv * (a.N + 1) + 4 * kMaxSide + static_cast<size_t>(a.N)) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k_gtau_propagate<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
   if (e != cudaSuccess) return e;
