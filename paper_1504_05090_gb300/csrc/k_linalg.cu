@@ -518,6 +518,18 @@ __global__ void __launch_bounds__(256) k_gtau_finalize(const double* bins, doubl
   const double* bg = bins + static_cast<size_t>(cl) * 2 * N;
   const double* by = bg + N;
   __shared__ double fr[kMaxN], hc[kMaxN], hs[kMaxN];
+  // cos and sin of the Lx (Ly) distinct phases 2 pi m / Lx, once per block
+  __shared__ double cxs[kMaxSide], sxs[kMaxSide], cys[kMaxSide], sys[kMaxSide];
+  if (threadIdx.x < Lx) {
+    const double ph = 2.0 * threadIdx.x / Lx;
+    cxs[threadIdx.x] = cospi(ph);
+    sxs[threadIdx.x] = sinpi(ph);
+  }
+  if (threadIdx.x < Ly) {
+    const double ph = 2.0 * threadIdx.x / Ly;
+    cys[threadIdx.x] = cospi(ph);
+    sys[threadIdx.x] = sinpi(ph);
+  }
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
     const int rx = r % Lx, ry = r / Lx;
     fr[r] = bg[r] + (((rx + ry) & 1) ? -by[r] : by[r]);
@@ -528,9 +540,9 @@ __global__ void __launch_bounds__(256) k_gtau_finalize(const double* bins, doubl
     const int kx = e % Lx, ry = e / Lx;
     double c = 0.0, s = 0.0;
     for (int rx = 0; rx < Lx; ++rx) {
-      const double ph = 2.0 * ((kx * rx) % Lx) / Lx;
-      c += cospi(ph) * fr[rx + Lx * ry];
-      s += sinpi(ph) * fr[rx + Lx * ry];
+      const int m = (kx * rx) % Lx;
+      c += cxs[m] * fr[rx + Lx * ry];
+      s += sxs[m] * fr[rx + Lx * ry];
     }
     hc[e] = c;
     hs[e] = s;
@@ -540,8 +552,8 @@ __global__ void __launch_bounds__(256) k_gtau_finalize(const double* bins, doubl
     const int kx = e % Lx, ky = e / Lx;
     double acc = 0.0;
     for (int ry = 0; ry < Ly; ++ry) {
-      const double ph = 2.0 * ((ky * ry) % Ly) / Ly;
-      acc += cospi(ph) * hc[kx + Lx * ry] - sinpi(ph) * hs[kx + Lx * ry];
+      const int m = (ky * ry) % Ly;
+      acc += cys[m] * hc[kx + Lx * ry] - sys[m] * hs[kx + Lx * ry];
     }
     out[static_cast<size_t>(cl) * N + e] = acc / (2.0 * N);
   }
