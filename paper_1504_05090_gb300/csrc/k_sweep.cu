@@ -20,6 +20,7 @@
 #include "kernels.h"
 
 namespace dqmc {
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // Initial Ising field: s = +1 iff word 0 of Philox(i + N*l, ~0, chain, 1) is odd.
@@ -611,28 +612,47 @@ __global__ void __launch_bounds__(256) k_kron_cols(T* X, KronArgs a) {
 // Drift check: drift[c] = max(drift[c], max|Gw - G64| / max|G64|), then the
 // working G is replaced by the stabilised one.  One CTA per chain.
 // ---------------------------------------------------------------------------
+// One cluster of kDriftCS CTAs per chain, each over an interleaved share of
+// the elements: max |Gw - G64| and max |G64| are taken on the bit patterns of
+// the absolute values (non-negative doubles order as integers), so the only
+// FP64 work per element is the conversion and the difference; non-finite
+// entries of G64 are left out of the maxima and flagged, an infinite
+// difference counts, a NaN difference does not (as fmax would have it).  CTA 0 combines the
+// partial maxima of the cluster through distributed shared memory.
+constexpr int kDriftCS = 2;
 template <typename T>
 __global__ void __launch_bounds__(256) k_drift_reset(const double* G64, T* Gw, int N, double* drift,
                                                     int* status) {
-  const int c = blockIdx.x;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = static_cast<int>(cl.block_rank());
+  const int c = blockIdx.x / kDriftCS;
   const size_t nn = static_cast<size_t>(N) * N;
   const double* g = G64 + c * nn;
   T* w = Gw + c * nn;
-  double md = 0.0, mg = 0.0;
+  unsigned long long md = 0ull, mg = 0ull;
   bool bad = false;
-  for (size_t e = threadIdx.x; e < nn; e += blockDim.x) {
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull;
+  for (size_t e = rank * blockDim.x + threadIdx.x; e < nn; e += kDriftCS * blockDim.x) {
     const double ge = g[e];
-    bad |= !isfinite(ge);
-    md = fmax(md, absd(static_cast<double>(w[e]) - ge));
-    mg = fmax(mg, absd(ge));
+    const unsigned long long ga = static_cast<unsigned long long>(__double_as_longlong(ge)) & kAbs;
+    if (ga >= 0x7FF0000000000000ull) {  // Inf or NaN
+      bad = true;
+    } else {
+      const unsigned long long da =
+          static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(w[e]) - ge)) & kAbs;
+      md = (da <= 0x7FF0000000000000ull && da > md) ? da : md;  // Inf counts, NaN not
+      mg = ga > mg ? ga : mg;
+    }
     w[e] = static_cast<T>(ge);
   }
-  __shared__ double s1[32], s2[32];
+  __shared__ unsigned long long s1[32], s2[32];
   __shared__ int sb;
   if (threadIdx.x == 0) sb = 0;
   for (int o = 16; o > 0; o >>= 1) {
-    md = fmax(md, __shfl_xor_sync(0xFFFFFFFFu, md, o));
-    mg = fmax(mg, __shfl_xor_sync(0xFFFFFFFFu, mg, o));
+    const unsigned long long m1 = __shfl_xor_sync(0xFFFFFFFFu, md, o);
+    const unsigned long long m2 = __shfl_xor_sync(0xFFFFFFFFu, mg, o);
+    md = m1 > md ? m1 : md;
+    mg = m2 > mg ? m2 : mg;
   }
   __syncthreads();
   if (bad) atomicOr(&sb, 1);
@@ -643,13 +663,27 @@ __global__ void __launch_bounds__(256) k_drift_reset(const double* G64, T* Gw, i
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int w2 = 1; w2 < static_cast<int>(blockDim.x >> 5); ++w2) {
-      md = fmax(md, s1[w2]);
-      mg = fmax(mg, s2[w2]);
+      md = s1[w2] > md ? s1[w2] : md;
+      mg = s2[w2] > mg ? s2[w2] : mg;
     }
-    const double dr = mg > 0.0 ? md / mg : md;
-    if (!(dr <= drift[c])) drift[c] = dr;  // also propagates NaN
+    s1[0] = md;
+    s2[0] = mg;
     if (sb) atomicExch(status, kDevNonFinite);
   }
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) {
+    for (int r = 1; r < kDriftCS; ++r) {
+      const unsigned long long m1 = *cl.map_shared_rank(&s1[0], r);
+      const unsigned long long m2 = *cl.map_shared_rank(&s2[0], r);
+      md = m1 > md ? m1 : md;
+      mg = m2 > mg ? m2 : mg;
+    }
+    const double mdd = __longlong_as_double(static_cast<long long>(md));
+    const double mgd = __longlong_as_double(static_cast<long long>(mg));
+    const double dr = mgd > 0.0 ? mdd / mgd : mdd;
+    if (!(dr <= drift[c])) drift[c] = dr;
+  }
+  cl.sync();  // the peers' shared memory stays until CTA 0 has read it
 }
 
 // ---------------------------------------------------------------------------
@@ -885,8 +919,18 @@ cudaError_t launch_kron_cols(T* X, int batch, const KronArgs& a, cudaStream_t st
 template <typename T>
 cudaError_t launch_drift_reset(const double* G64, T* Gw, int C, int N, double* drift, int* status,
                                cudaStream_t st) {
-  k_drift_reset<T><<<C, 256, 0, st>>>(G64, Gw, N, drift, status);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C * kDriftCS, 1, 1);
+  cfg.blockDim = dim3(256, 1, 1);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kDriftCS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_drift_reset<T>, G64, Gw, N, drift, status);
 }
 
 cudaError_t launch_observables(const double* G64, int C, int Lx, int Ly, double t, double* obs,
