@@ -235,8 +235,8 @@ DF32_PEAK = 2 * 152 * 128 * 2.07e9 / 14 / 1e12
 TRAFFIC = {
     # panel x 8, fused rank-32 products x 30, finalize: one blocked QR launch
     ("qr_pivot", None): (687.4e6, ("k_qr_blocked.cu", "k_ozaki.cu"), "aadad93db001c3cb"),
-    ("metropolis", "df32"): (33.69e6, ("k_sweep.cu",), "7cbb24368c12820d"),
-    ("stack_kron", None): (34.13e6, ("k_kron_tc.cu",), "5046ac778a31eae9"),
+    ("metropolis", "df32"): (33.70e6, ("k_sweep.cu",), "fec557e4b4b15359"),
+    ("stack_kron", None): (34.07e6, ("k_kron_tc.cu",), "5046ac778a31eae9"),
 }
 
 
