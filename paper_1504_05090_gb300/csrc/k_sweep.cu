@@ -106,6 +106,24 @@ __device__ __forceinline__ void delayed_flush(T* G, const T* U, const T* V, int 
 #pragma unroll
         for (int mm = 0; mm < MC; ++mm) v[mm] = (m0 + mm < cnt) ? V[(m0 + mm) * NP + j] : T(0);
       }
+      if constexpr (std::is_same<T, df32>::value && RB % 2 == 0) {
+        // two rows of U per 16-byte load when the row pair is 16-byte aligned
+        // (r0 even: U rows of NP entries start 16-byte aligned); the sums of
+        // each row see the same additions in the same order either way
+        if ((r0 & 1) == 0) {
+#pragma unroll
+          for (int q = 0; q < RB; q += 2) {
+#pragma unroll
+            for (int mm = 0; mm < MC; ++mm)
+              if (m0 + mm < cnt) {
+                const float4 u2 = *reinterpret_cast<const float4*>(U + (m0 + mm) * NP + r0 + q);
+                acc[q].add(df32(u2.x, u2.y), v[mm]);
+                acc[q + 1].add(df32(u2.z, u2.w), v[mm]);
+              }
+          }
+          continue;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < RB; ++q) {
 #pragma unroll
