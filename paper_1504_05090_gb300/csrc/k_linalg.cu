@@ -395,7 +395,14 @@ __global__ void k_convert(const double* src, T* dst, long long n) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N, const T* tx,
-                                 const T* ty, const T* pre, const T* post);
+                                 const T* ty, const T* txs, const T* tys, const T* pre,
+                                 const T* post);
+
+// Two taps read with one load (16 bytes for 8-byte types).
+template <typename T>
+struct alignas(2 * sizeof(T)) GtPair {
+  T a, b;
+};
 
 __device__ __forceinline__ double to_d(double x) { return x; }
 __device__ __forceinline__ double to_d(df32 x) { return static_cast<double>(x); }
@@ -416,12 +423,17 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
   T* tmp = v + nv * ld;
   T* tx = tmp + nv * ld;
   T* ty = tx + 2 * kMaxSide;
-  T* sc = ty + 2 * kMaxSide;
+  T* txs = ty + 2 * kMaxSide;  // the taps shifted by one, txs[k] = tx[k + 1]
+  T* tys = txs + 2 * kMaxSide;
+  T* sc = tys + 2 * kMaxSide;
   const bool inv = (a.kind == kBIT);
   if (threadIdx.x < 2 * kMaxSide) {  // each circulant row twice over (kron_transform_d)
     const int t = threadIdx.x, tx_ = t % a.Lx, ty_ = t % a.Ly;
     tx[t] = static_cast<T>(inv ? a.taps.exi[tx_] : a.taps.ex[tx_]);
     ty[t] = static_cast<T>(inv ? a.taps.eyi[ty_] : a.taps.ey[ty_]);
+    const int tx1 = (t + 1) % a.Lx, ty1 = (t + 1) % a.Ly;
+    txs[t] = static_cast<T>(inv ? a.taps.exi[tx1] : a.taps.ex[tx1]);
+    tys[t] = static_cast<T>(inv ? a.taps.eyi[ty1] : a.taps.ey[ty1]);
   }
   double* X = Xall + static_cast<size_t>(b) * a.mat_stride;
   for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
@@ -437,7 +449,7 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
       for (int i = threadIdx.x; i < N; i += blockDim.x)
         sc[i] = f[static_cast<size_t>(l - 1) * N + i] > 0 ? up : dn;
       __syncthreads();
-      kron_transform_d<T>(v, tmp, nrows, ld, a.Lx, a.Ly, N, tx, ty, sc, nullptr);
+      kron_transform_d<T>(v, tmp, nrows, ld, a.Lx, a.Ly, N, tx, ty, txs, tys, sc, nullptr);
     }
     // every vector has exactly one element per separation r: the thread of
     // bin r sums them over the block's vectors in the working precision and
@@ -461,7 +473,8 @@ __global__ void __launch_bounds__(256) k_gtau_propagate(double* Xall, GtauArgs a
 
 template <typename T>
 __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N, const T* tx,
-                                 const T* ty, const T* pre, const T* post) {
+                                 const T* ty, const T* txs, const T* tys, const T* pre,
+                                 const T* post) {
   const int tot = nv * N;
   if (pre) {  // diagonal factor applied once per element, not once per tap
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -469,6 +482,51 @@ __device__ void kron_transform_d(T* v, T* tmp, int nv, int ld, int Lx, int Ly, i
       v[vi * ld + i] *= pre[i];
     }
     __syncthreads();
+  }
+  if ((Lx & 1) == 0 && (Ly & 1) == 0) {
+    // Even sides: a thread takes two neighbouring outputs (x, x + 1) of one
+    // row (then (y, y + 1) of one column).  Both sums read the same input
+    // entry (one load), and their taps E[x - x'], E[x + 1 - x'] are adjacent:
+    // one 16-byte load from tx (tap index even) or from txs, the same taps
+    // shifted by one (odd).  Same additions in the same order per output.
+    const int hx = Lx >> 1, hy = Ly >> 1;
+    const int ptx = nv * Ly * hx;
+    for (int e = threadIdx.x; e < ptx; e += blockDim.x) {
+      const int vi = e / (Ly * hx), rr = e - vi * (Ly * hx), y = rr / hx, x = 2 * (rr - y * hx);
+      const T* row = v + vi * ld + Lx * y;
+      ProdSum<T> a0, a1;
+      for (int xp = 0; xp < Lx; ++xp) {
+        const int b = x + Lx - xp;  // tap index of output x; b + 1 that of x + 1
+        const GtPair<T> t2 = (b & 1) ? *reinterpret_cast<const GtPair<T>*>(txs + b - 1)
+                                       : *reinterpret_cast<const GtPair<T>*>(tx + b);
+        const T r = row[xp];
+        a0.add(t2.a, r);
+        a1.add(t2.b, r);
+      }
+      tmp[vi * ld + Lx * y + x] = a0.get();
+      tmp[vi * ld + Lx * y + x + 1] = a1.get();
+    }
+    __syncthreads();
+    const int pty = nv * hy * Lx;
+    for (int e = threadIdx.x; e < pty; e += blockDim.x) {
+      const int vi = e / (hy * Lx), rr = e - vi * (hy * Lx), yp2 = rr / Lx, x = rr - yp2 * Lx;
+      const int y = 2 * yp2;
+      const T* col = tmp + vi * ld + x;
+      ProdSum<T> a0, a1;
+      for (int yp = 0; yp < Ly; ++yp) {
+        const int b = y + Ly - yp;
+        const GtPair<T> t2 = (b & 1) ? *reinterpret_cast<const GtPair<T>*>(tys + b - 1)
+                                       : *reinterpret_cast<const GtPair<T>*>(ty + b);
+        const T c = col[Lx * yp];
+        a0.add(t2.a, c);
+        a1.add(t2.b, c);
+      }
+      const int i0 = x + Lx * y, i1 = i0 + Lx;
+      v[vi * ld + i0] = post ? a0.get() * post[i0] : a0.get();
+      v[vi * ld + i1] = post ? a1.get() * post[i1] : a1.get();
+    }
+    __syncthreads();
+    return;
   }
   // Two vectors per thread sharing each tap load; taps stored twice over
   // (tx[k] = Ex[k mod Lx] for k < 2 Lx), tap x - x' mod Lx = tx[x + Lx - x'].
@@ -626,7 +684,7 @@ template cudaError_t launch_convert<df32>(const double*, df32*, long long, cudaS
 template <typename T>
 static cudaError_t gtau_launch(double* X, int batch, const GtauArgs& a, cudaStream_t st) {
   const size_t sm =
-                    (2ull * a.nv * (a.N + 1) + 4 * kMaxSide + static_cast<size_t>(a.N)) * sizeof(T);
+                    (2ull * a.nv * (a.N + 1) + 8 * kMaxSide + static_cast<size_t>(a.N)) * sizeof(T);
   cudaError_t e = cudaFuncSetAttribute(k_gtau_propagate<T>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm));
   if (e != cudaSuccess) return e;

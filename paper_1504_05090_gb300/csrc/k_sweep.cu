@@ -440,10 +440,16 @@ __global__ void __launch_bounds__(256 * metro_halves<T>()) k_metropolis(T* Gall,
 // Kronecker transform of nv vectors held in shared memory (row stride ld):
 // v <- Ey (x) Ex applied to (pre o v), then multiplied by post.
 // ---------------------------------------------------------------------------
+// Two taps read with one load (16 bytes for 8-byte types).
+template <typename T>
+struct alignas(2 * sizeof(T)) KronPair {
+  T a, b;
+};
+
 template <typename T>
 __device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int Lx, int Ly, int N,
-                                               const T* tx, const T* ty, const T* pre,
-                                               const T* post) {
+                                               const T* tx, const T* ty, const T* txs,
+                                               const T* tys, const T* pre, const T* post) {
   const int tot = nv * N;
   if (pre) {  // diagonal factor applied once per element, not once per tap
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
@@ -451,6 +457,51 @@ __device__ __forceinline__ void kron_transform(T* v, T* tmp, int nv, int ld, int
       v[vi * ld + i] *= pre[i];
     }
     __syncthreads();
+  }
+  if ((Lx & 1) == 0 && (Ly & 1) == 0) {
+    // Even sides: a thread takes two neighbouring outputs (x, x + 1) of one
+    // row (then (y, y + 1) of one column).  Both sums read the same input
+    // entry (one load), and their taps E[x - x'], E[x + 1 - x'] are adjacent:
+    // one 16-byte load from tx (tap index even) or from txs, the same taps
+    // shifted by one (odd).  Same additions in the same order per output.
+    const int hx = Lx >> 1, hy = Ly >> 1;
+    const int ptx = nv * Ly * hx;
+    for (int e = threadIdx.x; e < ptx; e += blockDim.x) {
+      const int vi = e / (Ly * hx), rr = e - vi * (Ly * hx), y = rr / hx, x = 2 * (rr - y * hx);
+      const T* row = v + vi * ld + Lx * y;
+      ProdSum<T> a0, a1;
+      for (int xp = 0; xp < Lx; ++xp) {
+        const int b = x + Lx - xp;  // tap index of output x; b + 1 that of x + 1
+        const KronPair<T> t2 = (b & 1) ? *reinterpret_cast<const KronPair<T>*>(txs + b - 1)
+                                       : *reinterpret_cast<const KronPair<T>*>(tx + b);
+        const T r = row[xp];
+        a0.add(t2.a, r);
+        a1.add(t2.b, r);
+      }
+      tmp[vi * ld + Lx * y + x] = a0.get();
+      tmp[vi * ld + Lx * y + x + 1] = a1.get();
+    }
+    __syncthreads();
+    const int pty = nv * hy * Lx;
+    for (int e = threadIdx.x; e < pty; e += blockDim.x) {
+      const int vi = e / (hy * Lx), rr = e - vi * (hy * Lx), yp2 = rr / Lx, x = rr - yp2 * Lx;
+      const int y = 2 * yp2;
+      const T* col = tmp + vi * ld + x;
+      ProdSum<T> a0, a1;
+      for (int yp = 0; yp < Ly; ++yp) {
+        const int b = y + Ly - yp;
+        const KronPair<T> t2 = (b & 1) ? *reinterpret_cast<const KronPair<T>*>(tys + b - 1)
+                                       : *reinterpret_cast<const KronPair<T>*>(ty + b);
+        const T c = col[Lx * yp];
+        a0.add(t2.a, c);
+        a1.add(t2.b, c);
+      }
+      const int i0 = x + Lx * y, i1 = i0 + Lx;
+      v[vi * ld + i0] = post ? a0.get() * post[i0] : a0.get();
+      v[vi * ld + i1] = post ? a1.get() * post[i1] : a1.get();
+    }
+    __syncthreads();
+    return;
   }
   // A thread takes the same element of two vectors (2 vp, 2 vp + 1): the two
   // sums are independent and share every tap load.  The taps are stored twice
@@ -501,6 +552,8 @@ struct KronStage {
   T* tmp;
   T* tx;   // active taps x
   T* ty;   // active taps y
+  T* txs;  // the same taps shifted by one, txs[k] = tx[k + 1] (paired loads)
+  T* tys;
   T* sc;   // diag scale of the current slice
 };
 
@@ -511,7 +564,9 @@ __device__ __forceinline__ KronStage<T> kron_stage(unsigned char* raw, int nv, i
   s.tmp = s.v + nv * ld;
   s.tx = s.tmp + nv * ld;
   s.ty = s.tx + 2 * kMaxSide;
-  s.sc = s.ty + 2 * kMaxSide;
+  s.txs = s.ty + 2 * kMaxSide;
+  s.tys = s.txs + 2 * kMaxSide;
+  s.sc = s.tys + 2 * kMaxSide;
   return s;
 }
 
@@ -538,6 +593,9 @@ __device__ __forceinline__ void kron_load_taps(const KronArgs& a, KronStage<T> s
     const bool inv = (a.kind == kBIT);
     s.tx[t] = static_cast<T>(inv ? a.taps.exi[tx] : a.taps.ex[tx]);
     s.ty[t] = static_cast<T>(inv ? a.taps.eyi[ty] : a.taps.ey[ty]);
+    const int tx1 = (t + 1) % a.Lx, ty1 = (t + 1) % a.Ly;
+    s.txs[t] = static_cast<T>(inv ? a.taps.exi[tx1] : a.taps.ex[tx1]);
+    s.tys[t] = static_cast<T>(inv ? a.taps.eyi[ty1] : a.taps.ey[ty1]);
   }
 }
 
@@ -578,10 +636,10 @@ __global__ void __launch_bounds__(256) k_kron_rows(const T* in, T* out, KronArgs
     kron_load_scale(a, s, f + static_cast<size_t>(l0) * N, N);
     __syncthreads();
     if (a.kind == kBT)
-      kron_transform(s.v, s.tmp, nrows, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)nullptr,
+      kron_transform(s.v, s.tmp, nrows, ld, a.Lx, a.Ly, N, s.tx, s.ty, s.txs, s.tys, (const T*)nullptr,
                      (const T*)s.sc);
     else
-      kron_transform(s.v, s.tmp, nrows, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)s.sc,
+      kron_transform(s.v, s.tmp, nrows, ld, a.Lx, a.Ly, N, s.tx, s.ty, s.txs, s.tys, (const T*)s.sc,
                      (const T*)nullptr);
   }
   for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
@@ -614,10 +672,10 @@ __global__ void __launch_bounds__(256) k_kron_cols(T* X, KronArgs a) {
     kron_load_scale(a, s, f + static_cast<size_t>(l0) * N, N);
     __syncthreads();
     if (a.kind == kBT)
-      kron_transform(s.v, s.tmp, ncols, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)nullptr,
+      kron_transform(s.v, s.tmp, ncols, ld, a.Lx, a.Ly, N, s.tx, s.ty, s.txs, s.tys, (const T*)nullptr,
                      (const T*)s.sc);
     else
-      kron_transform(s.v, s.tmp, ncols, ld, a.Lx, a.Ly, N, s.tx, s.ty, (const T*)s.sc,
+      kron_transform(s.v, s.tmp, ncols, ld, a.Lx, a.Ly, N, s.tx, s.ty, s.txs, s.tys, (const T*)s.sc,
                      (const T*)nullptr);
   }
   for (int e = threadIdx.x; e < ncols * N; e += blockDim.x) {
@@ -909,7 +967,7 @@ cudaError_t launch_metropolis(T* G, int8_t* field, int C, const MetroArgs& a, cu
 
 template <typename T>
 size_t kron_smem(int N, int nv) {
-  return (2ull * nv * (N + 1) + 4 * kMaxSide + N) * sizeof(T);
+  return (2ull * nv * (N + 1) + 8 * kMaxSide + N) * sizeof(T);
 }
 
 template <typename T>
