@@ -235,7 +235,7 @@ DF32_PEAK = 2 * 152 * 128 * 2.07e9 / 14 / 1e12
 TRAFFIC = {
     # panel x 8, fused rank-32 products x 30, finalize: one blocked QR launch
     ("qr_pivot", None): (687.4e6, ("k_qr_blocked.cu", "k_ozaki.cu"), "aadad93db001c3cb"),
-    ("metropolis", "df32"): (33.71e6, ("k_sweep.cu",), "e0505e65d31e1c66"),
+    ("metropolis", "df32"): (33.71e6, ("k_sweep.cu",), "e10916f2f31b97b5"),
     ("stack_kron", None): (34.07e6, ("k_kron_tc.cu",), "5046ac778a31eae9"),
 }
 
